@@ -1,0 +1,174 @@
+"""TEST INFRASTRUCTURE ONLY: the exact CPU oracle for color-coding tree counting.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it and
+shares no code with it (``sgc_oracle.c`` is its own implementation of the
+paper's Section 2.1 color coding, Eq. 1 index, Eq. 2 pruning and the
+pre-computed neighbour traversal of Section 4.2).
+
+Counts are exact unsigned 128-bit integers (overflow is reported, never
+wrapped); Python receives them as ``int``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sgc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libsgc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, OVERFLOW, EINVAL, ENOMEM = 0, 1, -1, -2
+
+
+class OracleOverflow(ArithmeticError):
+    """A count exceeded 2**128 - 1."""
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libsgc_oracle.so`` in place (gcc -O2 -fopenmp)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            lib.oracle_color.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_uint8)]
+            lib.oracle_count.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32,
+                                         P(ctypes.c_int32), P(ctypes.c_uint8), ctypes.c_int32, ctypes.c_int32,
+                                         P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
+            lib.oracle_automorphisms.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_uint64)]
+            lib.oracle_colorset_index.argtypes = [P(ctypes.c_int32), ctypes.c_int32]
+            lib.oracle_colorset_index.restype = ctypes.c_int64
+            lib.oracle_colorset_unindex.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                    P(ctypes.c_int32)]
+            for f in (lib.oracle_color, lib.oracle_count, lib.oracle_automorphisms, lib.oracle_colorset_unindex,
+                      lib.oracle_threads):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _check(rc):
+    if rc == OVERFLOW:
+        raise OracleOverflow("oracle: a count exceeded the unsigned 128-bit range")
+    if rc == EINVAL:
+        raise ValueError("oracle: invalid argument")
+    if rc == ENOMEM:
+        raise MemoryError("oracle: out of host memory")
+    if rc != OK:
+        raise RuntimeError(f"oracle: error {rc}")
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_threads())
+
+
+def colors(seed: int, n: int, k: int) -> np.ndarray:
+    """Counter-based coloring: SplitMix64 draw v of stream ``seed``, hi32 scaled to [0, k)."""
+    out = np.empty(max(n, 1), dtype=np.uint8)
+    _check(_load().oracle_color(seed, n, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return out[:n]
+
+
+def colorset_index(cols) -> int:
+    """Eq. 1 index of an ascending color list."""
+    a, p = _i32(cols)
+    return int(_load().oracle_colorset_index(p, len(a)))
+
+
+def colorset_unindex(idx: int, h: int, k: int) -> list:
+    out = np.zeros(max(h, 1), dtype=np.int32)
+    _check(_load().oracle_colorset_unindex(idx, h, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return [int(x) for x in out[:h]]
+
+
+@dataclass
+class CountResult:
+    maps: int               # colorful injective maps T -> G  (sum_v N(v, T, all colors))
+    max_intermediate: int   # largest value in any table, buffer or the final sum
+    per_vertex: list | None = None
+
+
+def count(row_ptr, col_idx, parent, cols, mode: str = "pruned", root: int | None = None,
+          per_vertex: bool = False) -> CountResult:
+    """Exact colorful maps of tree ``parent`` in graph (row_ptr, col_idx) under coloring ``cols``."""
+    lib = _load()
+    rp, rpp = _i32(row_ptr)
+    ci, cip = _i32(col_idx if len(col_idx) else np.zeros(1, np.int32))
+    par, parp = _i32(parent)
+    col = np.ascontiguousarray(cols, dtype=np.uint8)
+    colp = (col if len(col) else np.zeros(1, np.uint8)).ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    n = len(rp) - 1
+    maps = (ctypes.c_uint64 * 2)()
+    mx = (ctypes.c_uint64 * 2)()
+    pv = np.zeros((max(n, 1), 2), dtype=np.uint64) if per_vertex else None
+    pvp = pv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if per_vertex else None
+    rc = lib.oracle_count(n, rpp, cip, len(par), parp, colp, {"pruned": 0, "literal": 1}[mode],
+                          -1 if root is None else int(root), maps, mx, pvp)
+    _check(rc)
+    res = CountResult(maps=int(maps[0]) | (int(maps[1]) << 64), max_intermediate=int(mx[0]) | (int(mx[1]) << 64))
+    if per_vertex:
+        res.per_vertex = [int(lo) | (int(hi) << 64) for lo, hi in pv[:n]]
+    return res
+
+
+def automorphisms(parent) -> int:
+    """|Aut(T)| as the colorful maps of T into itself under the identity coloring."""
+    par, parp = _i32(parent)
+    out = ctypes.c_uint64(0)
+    _check(_load().oracle_automorphisms(len(par), parp, ctypes.byref(out)))
+    return int(out.value)
+
+
+@dataclass
+class Estimate:
+    seeds: list
+    maps: list          # per coloring
+    copies: list        # maps / |Aut(T)| per coloring (exact)
+    estimates: list     # copies * k^k / k!  per coloring (float)
+    mean: float         # mean of the per-coloring estimates
+    aut: int
+    max_intermediate: int
+
+
+def estimate(row_ptr, col_idx, parent, seeds, mode: str = "pruned") -> Estimate:
+    """Per-coloring colorful counts and the color-coding estimate k^k/k! * copies, averaged."""
+    k = len(parent)
+    n = len(row_ptr) - 1
+    aut = automorphisms(parent)
+    scale = Fraction(k ** k, math.factorial(k))
+    maps, copies, ests = [], [], []
+    mx = 0
+    for s in seeds:
+        r = count(row_ptr, col_idx, parent, colors(int(s), n, k), mode=mode)
+        if r.maps % aut != 0:
+            raise ArithmeticError("oracle: maps not divisible by |Aut(T)|")
+        maps.append(r.maps)
+        copies.append(r.maps // aut)
+        ests.append(float(copies[-1] * scale))
+        mx = max(mx, r.max_intermediate)
+    mean = float(sum(Fraction(c) for c in copies) * scale / len(seeds)) if seeds else 0.0
+    return Estimate(list(seeds), maps, copies, ests, mean, aut, mx)
