@@ -1,0 +1,187 @@
+/*
+ * sgc.h - C ABI of libsgc, a GB300 (sm_103a) implementation of color-coding
+ * counting of non-induced tree templates (Chen et al., "A GraphBLAS Approach
+ * for Subgraph Counting", HPDC'19).
+ *
+ * One iteration of the method (Section 2.1) colors every vertex uniformly at
+ * random with k = |T| colors, counts the colorful embeddings of the template
+ * T by a dynamic program over sub-templates, and scales the count by
+ * k^k / k! (the inverse of the probability that a fixed copy is colorful).
+ * Each DP step for a sub-template T_s with active child T_a and passive child
+ * T_p is
+ *     P   = A * M_p                                   (SpMM, Eq. 2 and Section 4.5)
+ *     M_s(v, I(C)) = sum over splits C = C_a + C_p of
+ *                    M_a(v, I(C_a)) * P(v, I(C_p))    (eMA, Section 4.5)
+ * with color sets indexed by Eq. 1.  The last step reduces over vertices.
+ *
+ * Conventions for every function below:
+ *   - Return an sgc_status; SGC_OK is 0.  On failure sgc_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - Host pointers are only read during the call; inputs are copied.
+ *   - Handles are opaque, owned by the library, and released by the matching
+ *     *_destroy function (NULL is accepted and ignored).
+ *   - All device work runs on the GPU that was current when the graph was
+ *     created.  Calls on the same graph handle are serialised internally.
+ *   - There is no CPU fallback: if no CUDA device is usable, calls that need
+ *     one return SGC_ERR_CUDA.
+ */
+#ifndef SGC_H
+#define SGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sgc_status {
+  SGC_OK = 0,
+  SGC_ERR_INVALID = 1,     /* bad argument: malformed CSR, not a tree, k out of range ... */
+  SGC_ERR_OOM = 2,         /* device or host memory exhausted, or above options.mem_limit */
+  SGC_ERR_CUDA = 3,        /* a CUDA runtime error (message has the CUDA error string) */
+  SGC_ERR_TIMEOUT = 4,     /* a bounded wait ran out (server wait, device-side spin limit) */
+  SGC_ERR_OVERFLOW = 5,    /* a result is not representable (not expected for k <= 16) */
+  SGC_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
+  SGC_ERR_UNSUPPORTED = 7  /* valid request outside what this build supports */
+} sgc_status;
+
+/* Arithmetic of the count tables.  FP64 tables hold exact integers while
+ * every count stays below 2^53.  FP32 tables hold counts divided by a
+ * per-table power of two chosen on the device so nothing overflows; products
+ * are summed in FP32 inside SpMM and eMA and the final vertex reduction is
+ * FP64. */
+typedef enum sgc_precision { SGC_FP32 = 0, SGC_FP64 = 1 } sgc_precision;
+
+/* Largest template supported: C(16, 8) = 12870 color-set columns. */
+#define SGC_MAX_K 16
+
+typedef struct sgc_graph sgc_graph;
+typedef struct sgc_template sgc_template;
+
+/* Graph creation flags. */
+#define SGC_GRAPH_VALIDATE 1u   /* check CSR invariants on the device (recommended) */
+
+typedef struct sgc_options {
+  int32_t precision;   /* sgc_precision; default SGC_FP32 */
+  int32_t batch;       /* colorings evaluated together in one device pass; 0 = automatic */
+  int64_t mem_limit;   /* device workspace bytes this call may use; 0 = 90% of free memory */
+  void* stream;        /* cudaStream_t to run on; NULL = the graph's own stream */
+  int32_t root;        /* template vertex used as the DP root; -1 = cost-model choice */
+  int32_t use_graph;   /* 1 = replay the per-batch launch sequence as a CUDA graph (default) */
+} sgc_options;
+
+/* Fill *opt with the defaults described above. */
+void sgc_options_init(sgc_options* opt);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* sgc_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t sgc_version(void);
+
+/* ---------------------------------------------------------------- graphs -- */
+
+/*
+ * Create a graph from a host CSR adjacency (Section 4.3: the adjacency
+ * matrix A_G with A(i,j) = 1 for an edge).
+ *   n        vertices, 0 <= n < 2^31
+ *   nnz      stored entries = 2 * |E|
+ *   row_ptr  n+1 int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz
+ *   col_idx  nnz int32 in [0, n); each row strictly ascending (no
+ *            duplicates), no self-loops, and the matrix symmetric
+ *   flags    SGC_GRAPH_VALIDATE checks all of the above (SGC_ERR_INVALID)
+ * The library copies the CSR to the device, drops isolated vertices (they
+ * are in no embedding of a template with k >= 2) and renumbers the rest by
+ * degree, highest first; counts do not depend on vertex numbering.
+ */
+sgc_status sgc_graph_create(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                            uint32_t flags, sgc_graph** out);
+
+/* Same as sgc_graph_create, from device-resident CSR arrays (read on
+ * `stream`, a cudaStream_t or NULL; the caller keeps ownership). */
+sgc_status sgc_graph_create_device(int32_t n, int64_t nnz, const int32_t* d_row_ptr,
+                                   const int32_t* d_col_idx, uint32_t flags, void* stream,
+                                   sgc_graph** out);
+
+typedef struct sgc_graph_stats {
+  int32_t n;          /* vertices as given */
+  int32_t n_active;   /* vertices with degree > 0 (rows of every count table) */
+  int64_t nnz;        /* stored adjacency entries */
+  int32_t max_degree;
+  int32_t n_heavy;    /* rows whose neighbour list is split across warps in SpMM */
+  int32_t n_segments; /* neighbour-list segments of those rows */
+  int32_t device;     /* CUDA device ordinal */
+} sgc_graph_stats;
+
+sgc_status sgc_graph_stats_get(const sgc_graph* g, sgc_graph_stats* out);
+void sgc_graph_destroy(sgc_graph* g);
+
+/* ------------------------------------------------------------- templates -- */
+
+/*
+ * Create a tree template from a parent array (Section 2.1, item 2).
+ *   k       vertices, 1 <= k <= SGC_MAX_K
+ *   parent  k int32; exactly one entry is -1 (the given root), every other
+ *           entry is a vertex in [0, k), and the edges form one tree.
+ * The DP root and the order in which child edges are cut are chosen per
+ * count call by a cost model after Lemma 1 (or fixed by options.root);
+ * results do not depend on that choice.
+ */
+sgc_status sgc_template_create(int32_t k, const int32_t* parent, sgc_template** out);
+
+/* |Aut(T)|, the number of automorphisms of the (unrooted) template. */
+sgc_status sgc_template_automorphisms(const sgc_template* t, uint64_t* aut);
+void sgc_template_destroy(sgc_template* t);
+
+typedef struct sgc_plan_info {
+  int32_t root;            /* DP root used */
+  int32_t n_tables;        /* distinct sub-template count tables (isomorphic ones shared) */
+  int32_t n_spmm;          /* SpMM passes (one per distinct passive sub-template) */
+  int32_t n_ema;           /* eMA steps, including the final one */
+  int32_t batch;           /* colorings per device pass */
+  int64_t workspace_bytes; /* device workspace for one pass of `batch` colorings */
+  double est_bytes;        /* algorithmic HBM bytes per coloring (tables read/written once) */
+  double est_spmm_bytes;   /* of which SpMM (CSR + gathers counted once + outputs) */
+  double est_fma;          /* eMA multiply-adds per coloring */
+} sgc_plan_info;
+
+/* Describe the plan sgc_count would use for this graph, template and options. */
+sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_options* opt,
+                        sgc_plan_info* out);
+
+/* -------------------------------------------------------------- counting -- */
+
+/*
+ * Run n_iter color-coding iterations, one per seed.
+ *   seeds          n_iter host uint64 coloring seeds.  Vertex v (original
+ *                  numbering) gets color floor(hi32(x) * k / 2^32) where x is
+ *                  output number v of the SplitMix64 stream keyed by the seed
+ *                  (Steele, Lea and Flood 2014): x = mix(seed + (v+1) * 0x9E3779B97F4A7C15).
+ *   opt            NULL for defaults
+ *   estimate       out (host, may be NULL): mean over iterations of
+ *                  maps_i / |Aut(T)| * k^k / k!
+ *   colorful_maps  out (host, n_iter doubles, may be NULL): for each coloring
+ *                  the number of colorful injective edge-preserving maps
+ *                  T -> G, i.e. sum_v N(v, T, all colors) = |Aut(T)| * colorful copies.
+ *                  Exact in SGC_FP64 while every count is below 2^53.
+ * Blocks until the results are on the host.
+ */
+sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* seeds, int32_t n_iter,
+                     const sgc_options* opt, double* estimate, double* colorful_maps);
+
+/*
+ * Device-resident form of sgc_count for pipelines that keep everything on
+ * the GPU: seeds and colorful_maps are device pointers (n_iter each), the
+ * work is enqueued on opt->stream (or the graph's stream) and the call
+ * returns without synchronising.  The workspace stays owned by the graph;
+ * do not destroy the graph before the stream has finished.
+ */
+sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
+                            int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGC_H */

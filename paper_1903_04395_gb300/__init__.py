@@ -1,0 +1,258 @@
+"""Python binding of libsgc, the GB300 implementation of color-coding tree
+counting (Chen et al., "A GraphBLAS Approach for Subgraph Counting").
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+kernels of ``libsgc.so`` (see ``include/sgc.h`` for the C ABI this mirrors).
+The functions keep the C names (``sgc_graph_create``, ``sgc_count``, ...);
+``Graph``, ``Template`` and ``count`` are small conveniences on top.
+
+There is no CPU fallback: if ``libsgc.so`` has not been built, or no CUDA
+device is usable, calls raise ``SgcError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._build import LIB, build  # noqa: F401
+
+SGC_OK, SGC_ERR_INVALID, SGC_ERR_OOM, SGC_ERR_CUDA = 0, 1, 2, 3
+SGC_ERR_TIMEOUT, SGC_ERR_OVERFLOW, SGC_ERR_INTERNAL, SGC_ERR_UNSUPPORTED = 4, 5, 6, 7
+SGC_FP32, SGC_FP64 = 0, 1
+SGC_GRAPH_VALIDATE = 1
+SGC_MAX_K = 16
+
+_STATUS = {0: "SGC_OK", 1: "SGC_ERR_INVALID", 2: "SGC_ERR_OOM", 3: "SGC_ERR_CUDA", 4: "SGC_ERR_TIMEOUT",
+           5: "SGC_ERR_OVERFLOW", 6: "SGC_ERR_INTERNAL", 7: "SGC_ERR_UNSUPPORTED"}
+
+
+class SgcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class sgc_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("batch", ctypes.c_int32), ("mem_limit", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("root", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class sgc_graph_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_active", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("max_degree", ctypes.c_int32), ("n_heavy", ctypes.c_int32), ("n_segments", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class sgc_plan_info(ctypes.Structure):
+    _fields_ = [("root", ctypes.c_int32), ("n_tables", ctypes.c_int32), ("n_spmm", ctypes.c_int32),
+                ("n_ema", ctypes.c_int32), ("batch", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("est_bytes", ctypes.c_double), ("est_spmm_bytes", ctypes.c_double), ("est_fma", ctypes.c_double)]
+
+
+# exported symbols with their ctypes signatures (restype, argtypes)
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "sgc_options_init": (None, [_P(sgc_options)]),
+    "sgc_last_error": (ctypes.c_char_p, []),
+    "sgc_version": (ctypes.c_int32, []),
+    "sgc_graph_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P(ctypes.c_int32), _P(ctypes.c_int32),
+                                        ctypes.c_uint32, _P(_vp)]),
+    "sgc_graph_create_device": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_uint32, _vp,
+                                               _P(_vp)]),
+    "sgc_graph_stats_get": (ctypes.c_int, [_vp, _P(sgc_graph_stats)]),
+    "sgc_graph_destroy": (None, [_vp]),
+    "sgc_template_create": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(_vp)]),
+    "sgc_template_automorphisms": (ctypes.c_int, [_vp, _P(ctypes.c_uint64)]),
+    "sgc_template_destroy": (None, [_vp]),
+    "sgc_plan_get": (ctypes.c_int, [_vp, _vp, _P(sgc_options), _P(sgc_plan_info)]),
+    "sgc_count": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, _P(sgc_options),
+                                 _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "sgc_count_device": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsgc.so (built in-tree by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise SgcError(SGC_ERR_CUDA, f"{LIB} is not built; run paper_1903_04395_gb300.build()")
+        handle = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SGC_OK:
+        raise SgcError(rc, lib().sgc_last_error().decode(errors="replace"))
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    if a.size == 0:
+        a = np.zeros(1, dtype=np.int32)
+    return a, a.ctypes.data_as(_P(ctypes.c_int32))
+
+
+# ----------------------------------------------------------- C-named calls --
+
+def sgc_options_init(precision=SGC_FP32, batch=0, mem_limit=0, stream=None, root=-1, use_graph=1) -> sgc_options:
+    o = sgc_options()
+    lib().sgc_options_init(ctypes.byref(o))
+    o.precision, o.batch, o.mem_limit, o.root, o.use_graph = precision, batch, mem_limit, root, use_graph
+    o.stream = stream
+    return o
+
+
+def sgc_version() -> int:
+    return int(lib().sgc_version())
+
+
+def sgc_graph_create(n: int, nnz: int, row_ptr, col_idx, flags: int = SGC_GRAPH_VALIDATE) -> int:
+    rp, rpp = _i32(row_ptr)
+    ci, cip = _i32(col_idx)
+    out = _vp()
+    _check(lib().sgc_graph_create(n, nnz, rpp, cip, flags, ctypes.byref(out)))
+    return out.value
+
+
+def sgc_graph_create_device(n: int, nnz: int, d_row_ptr: int, d_col_idx: int, flags: int = SGC_GRAPH_VALIDATE,
+                            stream: int | None = None) -> int:
+    out = _vp()
+    _check(lib().sgc_graph_create_device(n, nnz, d_row_ptr, d_col_idx, flags, stream, ctypes.byref(out)))
+    return out.value
+
+
+def sgc_graph_stats_get(g: int) -> dict:
+    s = sgc_graph_stats()
+    _check(lib().sgc_graph_stats_get(g, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in sgc_graph_stats._fields_}
+
+
+def sgc_graph_destroy(g: int) -> None:
+    lib().sgc_graph_destroy(g)
+
+
+def sgc_template_create(k: int, parent) -> int:
+    p, pp = _i32(parent)
+    out = _vp()
+    _check(lib().sgc_template_create(k, pp, ctypes.byref(out)))
+    return out.value
+
+
+def sgc_template_automorphisms(t: int) -> int:
+    a = ctypes.c_uint64(0)
+    _check(lib().sgc_template_automorphisms(t, ctypes.byref(a)))
+    return int(a.value)
+
+
+def sgc_template_destroy(t: int) -> None:
+    lib().sgc_template_destroy(t)
+
+
+def sgc_plan_get(g: int, t: int, opt: sgc_options | None = None) -> dict:
+    info = sgc_plan_info()
+    _check(lib().sgc_plan_get(g, t, ctypes.byref(opt) if opt is not None else None, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in sgc_plan_info._fields_}
+
+
+def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None):
+    """Host-buffer count: returns (estimate, colorful maps per coloring as float64 array)."""
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    n = int(s.size)
+    maps = np.zeros(max(n, 1), dtype=np.float64)
+    est = ctypes.c_double(0.0)
+    _check(lib().sgc_count(g, t, s.ctypes.data_as(_P(ctypes.c_uint64)) if n else None, n,
+                           ctypes.byref(opt) if opt is not None else None, ctypes.byref(est),
+                           maps.ctypes.data_as(_P(ctypes.c_double))))
+    return float(est.value), maps[:n]
+
+
+def sgc_count_device(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:
+    """Device-buffer count: enqueue on opt.stream (or the graph's stream); no synchronisation."""
+    _check(lib().sgc_count_device(g, t, d_seeds, n_iter, ctypes.byref(opt) if opt is not None else None, d_maps))
+
+
+# -------------------------------------------------------------- wrappers --
+
+class Graph:
+    """Owning wrapper of an sgc_graph handle."""
+
+    def __init__(self, row_ptr, col_idx, validate: bool = True):
+        row_ptr = np.asarray(row_ptr)
+        n = len(row_ptr) - 1
+        self.handle = sgc_graph_create(n, len(col_idx), row_ptr, col_idx, SGC_GRAPH_VALIDATE if validate else 0)
+
+    @classmethod
+    def from_device(cls, n: int, nnz: int, d_row_ptr: int, d_col_idx: int, validate: bool = True, stream=None):
+        self = cls.__new__(cls)
+        self.handle = sgc_graph_create_device(n, nnz, d_row_ptr, d_col_idx,
+                                              SGC_GRAPH_VALIDATE if validate else 0, stream)
+        return self
+
+    def stats(self) -> dict:
+        return sgc_graph_stats_get(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Template:
+    """Owning wrapper of an sgc_template handle."""
+
+    def __init__(self, parent):
+        parent = np.asarray(parent, dtype=np.int32)
+        self.k = len(parent)
+        self.handle = sgc_template_create(self.k, parent)
+
+    @property
+    def automorphisms(self) -> int:
+        return sgc_template_automorphisms(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgc_template_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class CountResult:
+    estimate: float
+    maps: np.ndarray
+
+
+def count(graph: Graph, template: Template, seeds, precision: str = "fp32", batch: int = 0, root: int = -1,
+          mem_limit: int = 0) -> CountResult:
+    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root,
+                           mem_limit=mem_limit)
+    est, maps = sgc_count(graph.handle, template.handle, seeds, opt)
+    return CountResult(est, maps)
+
+
+def plan(graph: Graph, template: Template, precision: str = "fp32", batch: int = 0, root: int = -1) -> dict:
+    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root)
+    return sgc_plan_get(graph.handle, template.handle, opt)

@@ -1,0 +1,302 @@
+// graph.cu - graph handles: CSR validation on the device, removal of
+// isolated vertices, renumbering by degree (highest first) and the
+// neighbour-list segmentation of heavy rows used by SpMM and the histogram.
+//
+// The adjacency is the matrix A_G of Section 4.3 in CSR form.  Renumbering
+// does not change any count (counts are invariant under relabelling), and an
+// isolated vertex is in no embedding of a template with two or more vertices,
+// so count tables only hold rows for vertices of degree >= 1.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
+#include <vector>
+
+#include "sgc_internal.h"
+
+namespace sgc {
+namespace {
+
+enum : int32_t {
+  BAD_ROWPTR = 1,
+  BAD_COL = 2,
+  SELF_LOOP = 4,
+  UNSORTED = 8,
+  ASYMMETRIC = 16,
+};
+
+// row_ptr must be non-decreasing and inside [0, nnz]
+__global__ void k_check_rowptr(const int32_t* __restrict__ rp, int32_t n, int64_t nnz, int32_t* flags) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = rp[v], b = rp[v + 1];
+    if (a < 0 || b < a || b > nnz) atomicOr(flags, BAD_ROWPTR);
+  }
+}
+
+// one warp per row: range, self-loop, strictly ascending, and symmetry by
+// binary search of v in row u (rows are sorted once the previous checks pass)
+__global__ void k_check_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                             int32_t* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+    const int32_t lo = rp[v], hi = rp[v + 1];
+    int32_t f = 0;
+    for (int32_t e = lo + lane; e < hi; e += 32) {
+      const int32_t u = ci[e];
+      if (u < 0 || u >= n) { f |= BAD_COL; continue; }
+      if (u == v) f |= SELF_LOOP;
+      if (e > lo && ci[e - 1] >= u) f |= UNSORTED;
+      // symmetric: v must appear in row u
+      int32_t a = rp[u], b = rp[u + 1] - 1;
+      bool found = false;
+      int guard = 0;
+      while (a <= b && guard < 40) {
+        const int32_t mid = a + ((b - a) >> 1);
+        const int32_t x = ci[mid];
+        if (x == v) { found = true; break; }
+        if (x < v) a = mid + 1; else b = mid - 1;
+        ++guard;
+      }
+      if (!found) f |= ASYMMETRIC;
+    }
+    if (f) atomicOr(flags, f);
+  }
+}
+
+// new row v copies old row orig[v] with neighbours renamed through inv.
+// Column indices are range-checked here whatever the validation flags, so a
+// malformed CSR is reported instead of read out of bounds later; an entry
+// pointing at an isolated vertex (possible only without symmetry) is
+// reported the same way.
+__global__ void k_relabel(const int32_t* __restrict__ old_rp, const int32_t* __restrict__ old_ci, int32_t n,
+                          const int32_t* __restrict__ orig, const int32_t* __restrict__ inv,
+                          const int32_t* __restrict__ new_rp, int32_t n_act, int32_t* __restrict__ new_ci,
+                          int32_t* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_act; v += nw) {
+    const int32_t o = orig[v];
+    const int32_t lo = old_rp[o], deg = old_rp[o + 1] - lo, dst = new_rp[v];
+    for (int32_t j = lane; j < deg; j += 32) {
+      const int32_t u = old_ci[lo + j];
+      int32_t w = 0;
+      if (u < 0 || u >= n) {
+        atomicOr(flags, BAD_COL);
+      } else {
+        w = inv[u];
+        if (w < 0) { atomicOr(flags, ASYMMETRIC); w = 0; }
+      }
+      new_ci[dst + j] = w;
+    }
+  }
+}
+
+int default_seg_len() {
+  const char* s = std::getenv("SGC_SEG_LEN");
+  if (s) {
+    int v = std::atoi(s);
+    if (v >= 32 && v <= (1 << 20)) return v;
+  }
+  return 256;
+}
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void destroy_graph(sgc_graph* g) {
+  if (!g) return;
+  free_dev(g->d_row_ptr);
+  free_dev(g->d_col_idx);
+  free_dev(g->d_orig);
+  free_dev(g->d_seg_row);
+  free_dev(g->d_seg_lo);
+  free_dev(g->d_seg_hi);
+  free_dev(g->d_heavy_seg);
+  if (g->ws.ptr) cudaFree(g->ws.ptr);
+  g->ws.ptr = nullptr;
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+template <typename T>
+sgc_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
+  const size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(graph)");
+  if (!src.empty()) {
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(graph)");
+  }
+  return SGC_OK;
+}
+
+// Build the handle from device CSR (d_rp, d_ci) and the host copy of row_ptr.
+sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_t* d_ci,
+                       const std::vector<int32_t>& h_rp, uint32_t flags, cudaStream_t st, sgc_graph* g) {
+  int dev = 0, sms = 0;
+  SGC_CUDA_TRY(cudaGetDevice(&dev));
+  SGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  g->device = dev;
+  g->num_sms = sms;
+  g->n = n;
+  g->nnz = nnz;
+  // row_ptr is always checked (host side): everything below indexes with it
+  if (h_rp[0] != 0 || (int64_t)h_rp[n] != nnz)
+    return fail(SGC_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+  for (int32_t v = 0; v < n; ++v)
+    if (h_rp[v + 1] < h_rp[v]) return fail(SGC_ERR_INVALID, "row_ptr must be non-decreasing");
+  if (flags & SGC_GRAPH_VALIDATE) {
+    if (nnz % 2 != 0) return fail(SGC_ERR_INVALID, "an undirected simple graph has an even nnz");
+    int32_t* d_flags = nullptr;
+    SGC_CUDA_TRY(cudaMalloc(&d_flags, sizeof(int32_t)));
+    int32_t h_flags = 0;
+    cudaError_t e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess && n > 0) {
+      k_check_rowptr<<<std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(d_rp, n, nnz, d_flags);
+      k_check_cols<<<std::min<int64_t>((n + 7) / 8, 65536), 256, 0, st>>>(d_rp, d_ci, n, d_flags);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_flags);
+    if (e != cudaSuccess) return cuda_fail(e, "graph validation");
+    if (h_flags) {
+      std::string why;
+      if (h_flags & BAD_ROWPTR) why += " row_ptr out of range;";
+      if (h_flags & BAD_COL) why += " column index out of range;";
+      if (h_flags & SELF_LOOP) why += " self-loop;";
+      if (h_flags & UNSORTED) why += " row not strictly ascending (unsorted or duplicate);";
+      if (h_flags & ASYMMETRIC) why += " adjacency not symmetric;";
+      return fail(SGC_ERR_INVALID, "invalid CSR:" + why);
+    }
+  }
+  // degree order, highest first, ties by original id; degree-0 vertices dropped
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, h_rp[v + 1] - h_rp[v]);
+  std::vector<int64_t> bucket((size_t)maxd + 2, 0);
+  for (int32_t v = 0; v < n; ++v) bucket[(size_t)(maxd - (h_rp[v + 1] - h_rp[v]))]++;
+  int64_t run = 0;
+  for (auto& b : bucket) { int64_t c = b; b = run; run += c; }
+  std::vector<int32_t> order((size_t)n), inv((size_t)n, -1);
+  for (int32_t v = 0; v < n; ++v) order[(size_t)bucket[(size_t)(maxd - (h_rp[v + 1] - h_rp[v]))]++] = v;
+  int32_t n_act = 0;
+  while (n_act < n && h_rp[order[n_act] + 1] - h_rp[order[n_act]] > 0) ++n_act;
+  order.resize((size_t)n_act);
+  for (int32_t i = 0; i < n_act; ++i) inv[(size_t)order[i]] = i;
+  std::vector<int32_t> new_rp((size_t)n_act + 1, 0);
+  g->h_degree_sorted.resize((size_t)n_act);
+  for (int32_t i = 0; i < n_act; ++i) {
+    const int32_t d = h_rp[order[i] + 1] - h_rp[order[i]];
+    g->h_degree_sorted[(size_t)i] = d;
+    new_rp[(size_t)i + 1] = new_rp[(size_t)i] + d;
+  }
+  g->n_act = n_act;
+  g->max_deg = maxd;
+  g->seg_len = default_seg_len();
+  // heavy rows are a prefix; cut their neighbour lists into seg_len pieces
+  std::vector<int32_t> seg_row, seg_lo, seg_hi, heavy_seg(1, 0);
+  int32_t n_heavy = 0;
+  while (n_heavy < n_act && g->h_degree_sorted[(size_t)n_heavy] > g->seg_len) {
+    const int32_t lo = new_rp[(size_t)n_heavy], hi = new_rp[(size_t)n_heavy + 1];
+    for (int32_t s = lo; s < hi; s += g->seg_len) {
+      seg_row.push_back(n_heavy);
+      seg_lo.push_back(s);
+      seg_hi.push_back(std::min(hi, s + g->seg_len));
+    }
+    heavy_seg.push_back((int32_t)seg_row.size());
+    ++n_heavy;
+  }
+  g->n_heavy = n_heavy;
+  g->n_seg = (int32_t)seg_row.size();
+  sgc_status rc;
+  if ((rc = upload(&g->d_row_ptr, new_rp, st)) != SGC_OK) return rc;
+  if ((rc = upload(&g->d_orig, order, st)) != SGC_OK) return rc;
+  if ((rc = upload(&g->d_seg_row, seg_row, st)) != SGC_OK) return rc;
+  if ((rc = upload(&g->d_seg_lo, seg_lo, st)) != SGC_OK) return rc;
+  if ((rc = upload(&g->d_seg_hi, seg_hi, st)) != SGC_OK) return rc;
+  if ((rc = upload(&g->d_heavy_seg, heavy_seg, st)) != SGC_OK) return rc;
+  int32_t* d_inv = nullptr;
+  if ((rc = upload(&d_inv, inv, st)) != SGC_OK) return rc;
+  int32_t* d_flags = nullptr;
+  int32_t h_flags = 0;
+  cudaError_t e = cudaMalloc(&g->d_col_idx, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_flags, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess && n_act > 0) {
+    k_relabel<<<std::min<int64_t>((n_act + 7) / 8, 65536), 256, 0, st>>>(d_rp, d_ci, n, g->d_orig, d_inv,
+                                                                        g->d_row_ptr, n_act, g->d_col_idx, d_flags);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_inv);
+  if (d_flags) cudaFree(d_flags);
+  if (e != cudaSuccess) return cuda_fail(e, "graph relabel");
+  if (h_flags & BAD_COL) return fail(SGC_ERR_INVALID, "invalid CSR: column index out of range");
+  if (h_flags & ASYMMETRIC) return fail(SGC_ERR_INVALID, "invalid CSR: adjacency not symmetric");
+  return SGC_OK;
+}
+
+}  // namespace
+
+// Host CSR: copy to the device, then build.  Device CSR: read row_ptr back for
+// the host-side ordering, then build.  The raw copy is released either way.
+sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, bool on_device,
+                             uint32_t flags, cudaStream_t user_stream, sgc_graph** out) {
+  if (!out) return fail(SGC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 0 || nnz < 0 || nnz > INT32_MAX) return fail(SGC_ERR_INVALID, "n and nnz must be in [0, 2^31)");
+  if (!row_ptr || (nnz > 0 && !col_idx)) return fail(SGC_ERR_INVALID, "row_ptr/col_idx is NULL");
+  sgc_graph* g = new sgc_graph();
+  cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  cudaStream_t st = g->stream;
+  std::vector<int32_t> h_rp((size_t)n + 1);
+  int32_t* d_rp = nullptr;
+  int32_t* d_ci = nullptr;
+  sgc_status rc = SGC_OK;
+  if (on_device) {
+    if (user_stream) e = cudaStreamSynchronize(user_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "reading device row_ptr");
+    if (rc == SGC_OK) rc = build_graph(n, nnz, row_ptr, col_idx, h_rp, flags, st, g);
+  } else {
+    std::copy(row_ptr, row_ptr + n + 1, h_rp.begin());
+    e = cudaMalloc(&d_rp, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ci, sizeof(int32_t) * std::max<size_t>((size_t)nnz, 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0)
+      e = cudaMemcpyAsync(d_ci, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? fail(SGC_ERR_OOM, "device memory for the graph")
+                                                              : cuda_fail(e, "uploading the graph");
+    if (rc == SGC_OK) rc = build_graph(n, nnz, d_rp, d_ci, h_rp, flags, st, g);
+    cudaStreamSynchronize(st);
+    if (d_rp) cudaFree(d_rp);
+    if (d_ci) cudaFree(d_ci);
+  }
+  if (rc != SGC_OK) {
+    cudaStreamSynchronize(st);
+    destroy_graph(g);
+    return rc;
+  }
+  *out = g;
+  return SGC_OK;
+}
+
+void graph_destroy_impl(sgc_graph* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->stream);
+  destroy_graph(g);
+}
+
+}  // namespace sgc

@@ -1,0 +1,597 @@
+// kernels.cu - device side of one color-coding iteration (Section 2.1) in the
+// linear-algebra form of Section 4: per DP step an SpMM P = A * M_p (Eq. 2,
+// pre-computed neighbour traversal of Section 4.2, SpMM of Section 4.5) and
+// an element-wise multiply-add over the color-set splits (eMA, Section 4.5),
+// and at the last step a reduction over vertices.
+//
+// Layout in HBM.  Every table is vertex-major: the row of vertex v holds the
+// `batch` colorings one after the other, each ld entries wide (ld = number of
+// color sets padded to 16 bytes), i.e. element (v, b, I) sits at
+// ((v * batch + b) * ld + I).  SpMM therefore sees one wide row per vertex
+// (batch * ld columns, coalesced 16-byte gathers per neighbour) and the eMA
+// sees n * batch independent rows.  Padding columns are always written as 0.
+//
+// FP32 tables carry a power-of-two scale per table (ScaleState): stored value
+// = count * 2^-e.  Producers choose the shift from their inputs' measured
+// maxima so every stored value is at most 1 and no FP32 intermediate can
+// overflow; the final reduction multiplies in FP64 and applies 2^e.  FP64
+// tables are unscaled exact integers while below 2^53.
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "sgc_internal.h"
+
+namespace sgc {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float4 vadd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float vmax(float4 a) { return fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)); }
+__device__ __forceinline__ float vmax(double2) { return 0.f; }
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+
+// SplitMix64 output number v of the stream keyed by `seed` (Steele, Lea and
+// Flood 2014), high 32 bits scaled to [0, k).
+__device__ __forceinline__ uint32_t vertex_color(uint64_t seed, uint32_t v, uint32_t k) {
+  uint64_t z = seed + (uint64_t(v) + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (uint32_t)(((z >> 32) * (uint64_t)k) >> 32);
+}
+
+// 2^e as a float for |e| <= 126
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((127 + e) << 23);
+}
+
+// smallest s with bound * 2^-s < 1, for a finite bound >= 0
+__device__ __forceinline__ int shift_for(float bound) {
+  if (!(bound > 0.f)) return 0;
+  return ((__float_as_int(bound) >> 23) & 0xff) - 126;
+}
+
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+__device__ __forceinline__ void publish_max(ScaleState* st, float m) {
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&st->max_bits, __float_as_uint(m));
+}
+
+__device__ __forceinline__ float state_max(const ScaleState* st) { return __uint_as_float(st->max_bits); }
+
+// ------------------------------------------------------------ coloring --
+__global__ void k_color(const int32_t* __restrict__ orig, int64_t n_act, int batch,
+                        const uint64_t* __restrict__ seeds, int k, uint8_t* __restrict__ colors) {
+  const int64_t total = n_act * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / batch;
+    const int b = (int)(i - v * batch);
+    colors[i] = (uint8_t)vertex_color(seeds[b], (uint32_t)orig[v], (uint32_t)k);
+  }
+}
+
+// --------------------------------------- passive single vertex: histogram --
+// P(v, {c}) = number of neighbours of v with color c: the SpMM of A with the
+// one-hot leaf table N(u, {x}, {c}) = [c(u) = c], never materialised.
+// One warp per work item; items are the segments of heavy rows (counted with
+// integer atomics into hist_heavy) followed by the light rows.
+template <typename T>
+__global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                       const uint8_t* __restrict__ colors, int batch, int k, int32_t n_seg,
+                       const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo,
+                       const int32_t* __restrict__ seg_hi, int32_t n_heavy, int32_t n_act, T* __restrict__ H,
+                       int64_t ldh, int32_t* __restrict__ hist_heavy, ScaleState* st_out) {
+  extern __shared__ int32_t sh_hist[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bk = batch * k;
+  int32_t* h = sh_hist + warp * bk;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  const int64_t wpb = blockDim.x >> 5;
+  float wmax = 0.f;
+  for (int64_t item = blockIdx.x * wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    for (int i = lane; i < bk; i += 32) h[i] = 0;
+    __syncwarp();
+    const bool heavy = item < n_seg;
+    int32_t row, lo, hi;
+    if (heavy) {
+      row = seg_row[item];
+      lo = seg_lo[item];
+      hi = seg_hi[item];
+    } else {
+      row = n_heavy + (int32_t)(item - n_seg);
+      lo = row_ptr[row];
+      hi = row_ptr[row + 1];
+    }
+    for (int32_t e = lo + lane; e < hi; e += 32) {
+      const uint8_t* cu = colors + (int64_t)__ldg(col_idx + e) * batch;
+      for (int b = 0; b < batch; ++b) atomicAdd(&h[b * k + cu[b]], 1);
+    }
+    __syncwarp();
+    if (heavy) {
+      int32_t* dst = hist_heavy + (int64_t)row * bk;
+      for (int i = lane; i < bk; i += 32)
+        if (h[i]) atomicAdd(dst + i, h[i]);
+    } else {
+      T* out = H + (int64_t)row * batch * ldh;
+      for (int64_t i = lane; i < batch * ldh; i += 32) {
+        const int b = (int)(i / ldh);
+        const int c = (int)(i - b * ldh);
+        const int32_t cnt = c < k ? h[b * k + c] : 0;
+        out[i] = (T)cnt;
+        wmax = fmaxf(wmax, (float)cnt);
+      }
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, wmax);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, int32_t n_heavy, int batch, int k,
+                                 T* __restrict__ H, int64_t ldh, ScaleState* st_out) {
+  const int64_t total = (int64_t)n_heavy * batch * ldh;
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rb = i / ldh;
+    const int c = (int)(i - rb * ldh);
+    const int32_t cnt = c < k ? hist_heavy[rb * k + c] : 0;
+    H[i] = (T)cnt;
+    m = fmaxf(m, (float)cnt);
+  }
+  if (std::is_same<T, float>::value) publish_max(st_out, m);
+}
+
+// -------------------------------------------------------- SpMM P = A * M --
+// G lanes per work item, each lane owning NACC 16-byte column vectors of
+// the current column tile (blockIdx.y).  Items are heavy-row segments
+// (partial sums into `scratch`, reduced by k_spmm_reduce in segment order)
+// followed by the light rows (written straight to P).  Rows are numbered by
+// degree, highest first, so neighbour gathers concentrate on the hot rows.
+template <typename T, int G, int NACC>
+__global__ void __launch_bounds__(kBlock) k_spmm(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const T* __restrict__ M, int64_t ld_row, int64_t width,
+    T* __restrict__ P, T* __restrict__ scratch, const ScaleState* st_in, ScaleState* st_out) {
+  using V = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
+  const int gpb = blockDim.x / G;
+  const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+  const int64_t wv = width / VN;
+  const int64_t ldv = ld_row / VN;
+  const int64_t tile0 = (int64_t)blockIdx.y * G * NACC;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  const V* __restrict__ Mv = reinterpret_cast<const V*>(M);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)gpb + gid; item < nitems; item += (int64_t)gridDim.x * gpb) {
+    int32_t lo, hi;
+    V* dst;
+    bool heavy = item < n_seg;
+    if (heavy) {
+      lo = seg_lo[item];
+      hi = seg_hi[item];
+      dst = reinterpret_cast<V*>(scratch) + item * wv;
+    } else {
+      const int32_t row = n_heavy + (int32_t)(item - n_seg);
+      lo = row_ptr[row];
+      hi = row_ptr[row + 1];
+      dst = reinterpret_cast<V*>(P) + (int64_t)row * ldv;
+    }
+    V acc[NACC];
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) acc[i] = vzero<V>();
+    int32_t e = lo;
+    for (; e + 4 <= hi; e += 4) {
+      const int32_t u0 = __ldg(col_idx + e), u1 = __ldg(col_idx + e + 1);
+      const int32_t u2 = __ldg(col_idx + e + 2), u3 = __ldg(col_idx + e + 3);
+#pragma unroll
+      for (int i = 0; i < NACC; ++i) {
+        const int64_t cv = tile0 + i * G + gl;
+        if (cv < wv) {
+          const V x0 = __ldg(Mv + (int64_t)u0 * ldv + cv);
+          const V x1 = __ldg(Mv + (int64_t)u1 * ldv + cv);
+          const V x2 = __ldg(Mv + (int64_t)u2 * ldv + cv);
+          const V x3 = __ldg(Mv + (int64_t)u3 * ldv + cv);
+          acc[i] = vadd(acc[i], vadd(vadd(x0, x1), vadd(x2, x3)));
+        }
+      }
+    }
+    for (; e < hi; ++e) {
+      const int32_t u = __ldg(col_idx + e);
+#pragma unroll
+      for (int i = 0; i < NACC; ++i) {
+        const int64_t cv = tile0 + i * G + gl;
+        if (cv < wv) acc[i] = vadd(acc[i], __ldg(Mv + (int64_t)u * ldv + cv));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) {
+      const int64_t cv = tile0 + i * G + gl;
+      if (cv < wv) {
+        dst[cv] = acc[i];
+        if (!heavy) m = fmaxf(m, vmax(acc[i]));
+      }
+    }
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
+// heavy rows: P(h, :) = sum of the row's segment partials, in segment order
+template <typename T>
+__global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_heavy, const T* __restrict__ scratch,
+                              int64_t width, T* __restrict__ P, int64_t ld_row, ScaleState* st_out) {
+  using V = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
+  const int64_t wv = width / VN;
+  const int64_t total = (int64_t)n_heavy * wv;
+  const V* S = reinterpret_cast<const V*>(scratch);
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t h = i / wv, cv = i - h * wv;
+    V acc = vzero<V>();
+    for (int32_t s = heavy_seg[h]; s < heavy_seg[h + 1]; ++s) acc = vadd(acc, S[(int64_t)s * wv + cv]);
+    reinterpret_cast<V*>(P)[h * (ld_row / VN) + cv] = acc;
+    m = fmaxf(m, vmax(acc));
+  }
+  if (std::is_same<T, float>::value) publish_max(st_out, m);
+}
+
+// ------------------------------------ eMA with a single-vertex active child --
+// M_s(v, S) = [c(v) in S] * P(v, S \ {c(v)}): the split sum has one term.
+template <typename T>
+__global__ void k_gather(const uint8_t* __restrict__ colors, int64_t rows, const T* __restrict__ P, int64_t ldp,
+                         T* __restrict__ out, int64_t ldt, int64_t ct, const uint32_t* __restrict__ tab,
+                         const ScaleState* st_p, ScaleState* st_out) {
+  float scale = 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    s = shift_for(state_max(st_p));
+    scale = pow2f(-s);
+  }
+  const int64_t total = rows * ldt;
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / ldt;
+    const int64_t col = i - row * ldt;
+    T val = T(0);
+    if (col < ct) {
+      const uint32_t j = __ldg(tab + (int64_t)colors[row] * ct + col);
+      if (j != 0xFFFFFFFFu) val = P[row * ldp + j] * (T)scale;
+    }
+    out[i] = val;
+    m = fmaxf(m, (float)val);
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_p->e + s;
+  }
+}
+
+// ------------------------------------------------------- general eMA --
+// M_s(v, S) = sum over the binom(t, p) splits (A, S \ A) of M_a(v, A) * P(v, S \ A).
+// A block stages R consecutive rows of M_a and P in shared memory, transposed
+// (column-major inside the tile, stride R+1) so that lanes of a warp - one
+// row each - read consecutive banks; the split table entry is the same for
+// the lanes that share an output column (broadcast).
+template <typename T, int R>
+__global__ void __launch_bounds__(kBlock) k_ema(
+    const T* __restrict__ Ma, int64_t lda, int ca, const T* __restrict__ P, int64_t ldp, int cp,
+    T* __restrict__ out, int64_t ldt, int ct, const uint32_t* __restrict__ tab, int nsplit, int64_t rows,
+    const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sA = reinterpret_cast<T*>(sm_raw);
+  T* sP = sA + (int64_t)ca * (R + 1);
+  constexpr int NSUB = 32 / R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int r = lane % R, sub = lane / R;
+  float scale = 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    const float bound = (float)nsplit * state_max(st_a) * state_max(st_p);
+    s = shift_for(bound);
+    scale = pow2f(-s);
+  }
+  float m = 0.f;
+  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
+    const int nr = (int)(rows - r0 < R ? rows - r0 : R);
+    __syncthreads();
+    for (int i = threadIdx.x; i < R * ca; i += blockDim.x) {
+      const int rr = i / ca, c = i - rr * ca;
+      sA[c * (R + 1) + rr] = rr < nr ? Ma[(r0 + rr) * lda + c] : T(0);
+    }
+    for (int i = threadIdx.x; i < R * cp; i += blockDim.x) {
+      const int rr = i / cp, c = i - rr * cp;
+      sP[c * (R + 1) + rr] = rr < nr ? P[(r0 + rr) * ldp + c] : T(0);
+    }
+    __syncthreads();
+    for (int S = warp * NSUB + sub; S < ldt; S += nwarp * NSUB) {
+      T acc = T(0);
+      if (S < ct) {
+        int j = 0;
+        for (; j + 4 <= nsplit; j += 4) {
+          const uint32_t e0 = __ldg(tab + (int64_t)j * ct + S);
+          const uint32_t e1 = __ldg(tab + (int64_t)(j + 1) * ct + S);
+          const uint32_t e2 = __ldg(tab + (int64_t)(j + 2) * ct + S);
+          const uint32_t e3 = __ldg(tab + (int64_t)(j + 3) * ct + S);
+          acc += sA[(e0 & 0xFFFF) * (R + 1) + r] * sP[(e0 >> 16) * (R + 1) + r];
+          acc += sA[(e1 & 0xFFFF) * (R + 1) + r] * sP[(e1 >> 16) * (R + 1) + r];
+          acc += sA[(e2 & 0xFFFF) * (R + 1) + r] * sP[(e2 >> 16) * (R + 1) + r];
+          acc += sA[(e3 & 0xFFFF) * (R + 1) + r] * sP[(e3 >> 16) * (R + 1) + r];
+        }
+        for (; j < nsplit; ++j) {
+          const uint32_t e0 = __ldg(tab + (int64_t)j * ct + S);
+          acc += sA[(e0 & 0xFFFF) * (R + 1) + r] * sP[(e0 >> 16) * (R + 1) + r];
+        }
+        acc *= (T)scale;
+      }
+      if (r < nr) out[(r0 + r) * ldt + S] = acc;
+      m = fmaxf(m, (float)acc);
+    }
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_a->e + st_p->e + s;
+  }
+}
+
+// ----------------------------------------------- last step + vertex sum --
+// maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p), products and sums in
+// FP64.  Warp w of the fixed grid takes rows w, w + W, ... (W a multiple of
+// the batch, so a warp always sees the same coloring); per-block partials per
+// coloring are then summed in block order by k_final_sum: the result does
+// not depend on scheduling.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int64_t lda, const T* __restrict__ P,
+                                                  int64_t ldp, int cp, const uint32_t* __restrict__ tab,
+                                                  int64_t rows, int batch, double* __restrict__ partials) {
+  __shared__ double wacc[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  double acc = 0.0;
+  for (int64_t row = gw; row < rows; row += W) {
+    double v = 0.0;
+    for (int i = lane; i < cp; i += 32)
+      v += (double)Ma[row * lda + __ldg(tab + i)] * (double)P[row * ldp + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc += v;
+  }
+  if (lane == 0) wacc[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x < batch) {
+    // warps of this block with coloring b are those with (gw mod batch) == b
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) {
+      const int64_t g = (int64_t)blockIdx.x * nw + w;
+      if ((int)(g % batch) == (int)threadIdx.x) s += wacc[w];
+    }
+    partials[(int64_t)blockIdx.x * batch + threadIdx.x] = s;
+  }
+}
+
+// last step with a single-vertex active child: maps_b = sum_v P(v, [k] \ {c(v)})
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_final_leaf(const uint8_t* __restrict__ colors, const T* __restrict__ P,
+                                                       int64_t ldp, const uint32_t* __restrict__ tab, int64_t rows,
+                                                       int batch, double* __restrict__ partials) {
+  __shared__ double tacc[kBlock];
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;  // multiple of batch
+  double acc = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S)
+    acc += (double)P[row * ldp + __ldg(tab + colors[row])];
+  tacc[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < batch) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += batch) s += tacc[i];
+    partials[(int64_t)blockIdx.x * batch + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_final_sum(const double* __restrict__ partials, int nblocks, int batch, const ScaleState* st_a,
+                            const ScaleState* st_p, int fp32, double* __restrict__ out) {
+  const int b = threadIdx.x;
+  if (b >= batch) return;
+  double s = 0.0;
+  for (int i = 0; i < nblocks; ++i) s += partials[(int64_t)i * batch + b];
+  if (fp32) {
+    const int e = (st_a ? st_a->e : 0) + st_p->e;
+    s = ldexp(s, e);
+  }
+  out[b] = s;
+}
+
+template <typename KernelT>
+void allow_smem(KernelT kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int grid_for(int64_t work, int per_block, int cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <typename T, int G, int NACC>
+void launch_spmm_g(dim3 grid, cudaStream_t st, const sgc_graph* g, const T* M, int64_t ld_row, int64_t width, T* P,
+                   T* scratch, const ScaleState* si, ScaleState* so) {
+  k_spmm<T, G, NACC><<<grid, kBlock, 0, st>>>(g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo,
+                                              g->d_seg_hi, g->n_heavy, g->n_act, M, ld_row, width, P, scratch, si, so);
+}
+
+template <typename T, int G>
+void launch_spmm_n(int nacc, dim3 grid, cudaStream_t st, const sgc_graph* g, const T* M, int64_t ld_row,
+                   int64_t width, T* P, T* scratch, const ScaleState* si, ScaleState* so) {
+  switch (nacc) {
+    case 1: launch_spmm_g<T, G, 1>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
+    case 2: launch_spmm_g<T, G, 2>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
+    case 4: launch_spmm_g<T, G, 4>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
+    default: launch_spmm_g<T, G, 8>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
+  }
+}
+
+template <typename T>
+void launch_spmm(const sgc_graph* g, const T* M, int64_t width, T* P, T* scratch, const ScaleState* si,
+                 ScaleState* so, int num_sms, cudaStream_t st) {
+  constexpr int VN = Vec16<T>::n;
+  const int64_t wv = width / VN;
+  int G = 4;
+  while (G < 32 && G < wv) G *= 2;
+  int nacc = 1;
+  while (nacc < 8 && (int64_t)G * nacc < wv) nacc *= 2;
+  const int64_t tiles = (wv + (int64_t)G * nacc - 1) / ((int64_t)G * nacc);
+  const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+  const int gpb = kBlock / G;
+  dim3 grid((unsigned)grid_for(nitems, gpb, 1 << 30), (unsigned)tiles);
+  switch (G) {
+    case 4: launch_spmm_n<T, 4>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    case 8: launch_spmm_n<T, 8>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    case 16: launch_spmm_n<T, 16>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    default: launch_spmm_n<T, 32>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+  }
+  if (g->n_heavy > 0) {
+    k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * wv, kBlock, 16 * num_sms), kBlock, 0, st>>>(
+        g->d_heavy_seg, g->n_heavy, scratch, width, P, width, so);
+  }
+  (void)num_sms;
+}
+
+template <typename T, int R>
+void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
+                  const ScaleState* sa, const ScaleState* sp, ScaleState* so, int num_sms, cudaStream_t st) {
+  const size_t smem = (size_t)(op.cols_a + op.cols_p) * (R + 1) * sizeof(T);
+  allow_smem(k_ema<T, R>, smem);
+  const int64_t tiles = (rows + R - 1) / R;
+  const int grid = grid_for(tiles, 1, 1 << 30);
+  k_ema<T, R><<<grid, kBlock, smem, st>>>(Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out,
+                                          (int)op.cols_out, tab, (int)op.nsplit, rows, sa, sp, so);
+  (void)num_sms;
+}
+
+template <typename T>
+sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
+                      const ScaleState* sa, const ScaleState* sp, ScaleState* so, int num_sms, size_t smem_cap,
+                      cudaStream_t st) {
+  const size_t per = (size_t)(op.cols_a + op.cols_p) * sizeof(T);
+  if (per * 33 <= smem_cap) launch_ema_r<T, 32>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else if (per * 17 <= smem_cap) launch_ema_r<T, 16>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else if (per * 9 <= smem_cap) launch_ema_r<T, 8>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else if (per * 5 <= smem_cap) launch_ema_r<T, 4>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else if (per * 3 <= smem_cap) launch_ema_r<T, 2>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else if (per * 2 <= smem_cap) launch_ema_r<T, 1>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
+  else return fail(SGC_ERR_UNSUPPORTED, "eMA row does not fit in shared memory");
+  return SGC_OK;
+}
+
+template <typename T>
+sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t st) {
+  int dev = 0, num_sms = 0, smem_optin = 0;
+  SGC_CUDA_TRY(cudaGetDevice(&dev));
+  SGC_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  SGC_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t smem_cap = (size_t)smem_optin;
+  auto buf = [&](int b) -> char* { return ws + plan.bufs[b].offset; };
+  const int B = plan.batch;
+  const int64_t rows = plan.rows;
+  ScaleState* states = reinterpret_cast<ScaleState*>(buf(plan.buf_states));
+  auto S = [&](int i) -> ScaleState* { return i < 0 ? nullptr : states + i; };
+  const uint8_t* colors = reinterpret_cast<const uint8_t*>(buf(plan.buf_colors));
+  T* scratch = reinterpret_cast<T*>(buf(plan.buf_scratch));
+  double* partials = reinterpret_cast<double*>(buf(plan.buf_partials));
+  double* outv = reinterpret_cast<double*>(buf(plan.buf_out));
+  const bool fp32 = std::is_same<T, float>::value;
+
+  if (fp32) SGC_CUDA_TRY(cudaMemsetAsync(states, 0, sizeof(ScaleState) * (size_t)std::max(1, plan.n_states), st));
+  for (const PlanOp& op : plan.ops) {
+    switch (op.kind) {
+      case OP_COLOR:
+        k_color<<<grid_for(rows, kBlock, 8 * num_sms), kBlock, 0, st>>>(
+            g->d_orig, g->n_act, B, reinterpret_cast<const uint64_t*>(buf(plan.buf_seeds)), plan.k,
+            reinterpret_cast<uint8_t*>(buf(plan.buf_colors)));
+        break;
+      case OP_HIST: {
+        T* H = reinterpret_cast<T*>(buf(op.out));
+        int32_t* hh = reinterpret_cast<int32_t*>(buf(plan.buf_hist_heavy));
+        if (g->n_heavy > 0)
+          SGC_CUDA_TRY(cudaMemsetAsync(hh, 0, sizeof(int32_t) * (size_t)g->n_heavy * B * plan.k, st));
+        const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+        const size_t smem = (size_t)(kBlock / 32) * B * plan.k * sizeof(int32_t);
+        allow_smem(k_hist<T>, smem);
+        k_hist<T><<<grid_for(nitems, kBlock / 32, 1 << 30), kBlock, smem, st>>>(
+            g->d_row_ptr, g->d_col_idx, colors, B, plan.k, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi,
+            g->n_heavy, g->n_act, H, op.ld_out, hh, S(op.state_out));
+        if (g->n_heavy > 0)
+          k_hist_heavy_out<T><<<grid_for((int64_t)g->n_heavy * B * op.ld_out, kBlock, 8 * num_sms), kBlock, 0, st>>>(
+              hh, g->n_heavy, B, plan.k, H, op.ld_out, S(op.state_out));
+        break;
+      }
+      case OP_SPMM:
+        launch_spmm<T>(g, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p * B, reinterpret_cast<T*>(buf(op.out)),
+                       scratch, S(op.state_p), S(op.state_out), num_sms, st);
+        break;
+      case OP_GATHER:
+        k_gather<T><<<grid_for(rows * op.ld_out, kBlock, 16 * num_sms), kBlock, 0, st>>>(
+            colors, rows, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, reinterpret_cast<T*>(buf(op.out)),
+            op.ld_out, op.cols_out, d_tabs + op.tab_off, S(op.state_p), S(op.state_out));
+        break;
+      case OP_EMA: {
+        sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
+                                      reinterpret_cast<const T*>(buf(op.in_p)), reinterpret_cast<T*>(buf(op.out)),
+                                      d_tabs + op.tab_off, rows, S(op.state_a), S(op.state_p), S(op.state_out),
+                                      num_sms, smem_cap, st);
+        if (rc != SGC_OK) return rc;
+        break;
+      }
+      case OP_FINAL_LEAF:
+        k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(colors, reinterpret_cast<const T*>(buf(op.in_p)),
+                                                              op.ld_p, d_tabs + op.tab_off, rows, B, partials);
+        k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
+        break;
+      case OP_FINAL:
+        k_final<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)), op.ld_a,
+                                                         reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
+                                                         (int)op.cols_p, d_tabs + op.tab_off, rows, B, partials);
+        k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, S(op.state_a), S(op.state_p), fp32 ? 1 : 0,
+                                      outv);
+        break;
+    }
+  }
+  SGC_CUDA_TRY(cudaGetLastError());
+  return SGC_OK;
+}
+
+}  // namespace
+
+sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t stream) {
+  if (plan.precision == SGC_FP64) return run_pass_t<double>(g, plan, d_tabs, ws, stream);
+  return run_pass_t<float>(g, plan, d_tabs, ws, stream);
+}
+
+}  // namespace sgc

@@ -1,0 +1,162 @@
+// sgc_internal.h - shared declarations of libsgc's host planner, executor and
+// kernels.  Not part of the public ABI (include/sgc.h is).
+#pragma once
+
+#include <cstdint>
+#include <array>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sgc.h"
+
+namespace sgc {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+sgc_status fail(sgc_status st, const std::string& msg);
+sgc_status cuda_fail(cudaError_t e, const char* what);
+
+#define SGC_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::sgc::cuda_fail(_e, #expr); \
+  } while (0)
+
+// ------------------------------------------------ color-set index (Eq. 1)
+// Columns of a count table for sub-templates of size h are the h-subsets of
+// the k colors, numbered by Eq. 1: I(C) = sum_i binom(c_i, i) with the colors
+// ascending and i counted from 1 (the combinatorial number system, colex
+// order).
+struct ColorIndex {
+  int k = 0;
+  uint64_t binom[SGC_MAX_K + 2][SGC_MAX_K + 2] = {};
+  explicit ColorIndex(int k_);
+  uint64_t nsets(int h) const { return (h < 0 || h > k) ? 0 : binom[k][h]; }
+  // rank of a subset given as a bit mask over colors 0..k-1
+  uint32_t rank_mask(uint32_t mask) const;
+  // subset (bit mask) of size h with rank r
+  uint32_t unrank_mask(uint64_t r, int h) const;
+};
+
+// ------------------------------------------------------------------ graph
+struct Arena {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sgc
+
+struct sgc_graph {
+  int device = 0;
+  int num_sms = 0;
+  int32_t n = 0;          // vertices as given
+  int32_t n_act = 0;      // vertices with degree > 0, renumbered by degree (desc)
+  int64_t nnz = 0;
+  int32_t max_deg = 0;
+  int32_t seg_len = 0;    // neighbour-list segment length for heavy rows
+  int32_t n_heavy = 0;    // rows 0..n_heavy-1 have degree > seg_len
+  int32_t n_seg = 0;      // segments covering the heavy rows
+  int32_t* d_row_ptr = nullptr;   // n_act + 1
+  int32_t* d_col_idx = nullptr;   // nnz, new numbering
+  int32_t* d_orig = nullptr;      // n_act: original id of each new vertex
+  int32_t* d_seg_row = nullptr;   // n_seg: heavy row of each segment
+  int32_t* d_seg_lo = nullptr;    // n_seg: first CSR entry of each segment
+  int32_t* d_seg_hi = nullptr;    // n_seg: one past the last CSR entry
+  int32_t* d_heavy_seg = nullptr; // n_heavy + 1: first segment of each heavy row
+  cudaStream_t stream = nullptr;
+  // cached workspace, grown on demand, used by one call at a time
+  mutable std::mutex mu;
+  mutable sgc::Arena ws;
+  std::vector<int32_t> h_degree_sorted;  // degrees in new numbering (host copy)
+};
+
+struct sgc_template {
+  int32_t k = 0;
+  std::vector<int32_t> parent;
+  std::vector<std::vector<int32_t>> adj;
+  uint64_t aut = 0;
+  // device copies of the plan index tables, keyed by (device, root, policy)
+  mutable std::mutex mu;
+  mutable std::vector<std::pair<std::array<int, 3>, uint32_t*>> tab_cache;
+};
+
+namespace sgc {
+
+// ------------------------------------------------------------------- plan
+enum OpKind : int32_t {
+  OP_COLOR = 0,      // colors of every (vertex, coloring)
+  OP_HIST = 1,       // P for a single-vertex passive child: neighbour color histogram
+  OP_SPMM = 2,       // P = A * M_p
+  OP_GATHER = 3,     // eMA with a single-vertex active child
+  OP_EMA = 4,        // general eMA over the split table
+  OP_FINAL_LEAF = 5, // last step, single-vertex active child, fused with the vertex sum
+  OP_FINAL = 6,      // last step, general, fused with the vertex sum
+};
+
+struct PlanBuffer {
+  std::string name;
+  int64_t bytes = 0;
+  int64_t offset = 0;
+  int first = 0, last = 0;  // op indices of first and last use
+};
+
+struct PlanOp {
+  OpKind kind;
+  int out = -1;       // buffer written
+  int in_a = -1;      // active table buffer (EMA, FINAL)
+  int in_p = -1;      // passive table (SPMM input) or P buffer (GATHER, EMA, FINAL)
+  int t = 0, a = 0, p = 0;   // sub-template sizes
+  int64_t cols_out = 0, ld_out = 0;
+  int64_t cols_a = 0, ld_a = 0;
+  int64_t cols_p = 0, ld_p = 0;
+  int64_t nsplit = 0;        // binom(t, p)
+  int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
+  int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
+};
+
+struct Plan {
+  int k = 0, root = 0, batch = 1, precision = SGC_FP32, policy = 0;
+  int elem = 4;              // bytes per table entry
+  int64_t rows = 0;          // n_act * batch
+  std::vector<PlanBuffer> bufs;
+  std::vector<PlanOp> ops;
+  std::vector<uint32_t> tabs;  // all index tables, concatenated
+  int n_states = 0;
+  int n_tables = 0, n_spmm = 0, n_ema = 0;
+  int64_t ws_bytes = 0;
+  // per-coloring algorithmic traffic (bytes) and eMA FMAs
+  double est_bytes = 0, est_spmm_bytes = 0, est_fma = 0, est_cost = 0;
+  // fixed buffers
+  int buf_colors = -1, buf_seeds = -1, buf_out = -1, buf_states = -1, buf_partials = -1;
+  int buf_scratch = -1, buf_hist_heavy = -1;
+  int final_blocks = 0;
+  int64_t scratch_width = 0;
+};
+
+// Plan the DP for template t on graph g.  root < 0 and policy < 0 let the
+// cost model choose; batch is the number of colorings per pass.  Index tables
+// are only built when build_tabs is set.
+sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
+                     bool build_tabs, Plan* out);
+
+uint64_t automorphisms(const sgc_template* t);
+
+sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, bool on_device,
+                             uint32_t flags, cudaStream_t user_stream, sgc_graph** out);
+void graph_destroy_impl(sgc_graph* g);
+
+// -------------------------------------------------------------- kernels
+struct ScaleState {
+  int32_t e;          // table value = count * 2^-e  (FP32 path)
+  uint32_t max_bits;  // bits of the largest stored value (non-negative float)
+};
+
+// Executes one pass of `plan` for plan.batch colorings whose seeds are in
+// the workspace; writes plan.batch doubles (colorful maps) to the out buffer.
+sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws,
+                    cudaStream_t stream);
+
+}  // namespace sgc

@@ -1,0 +1,87 @@
+"""The C-ABI library (no GPU needed): it builds for sm_103a, loads, exports
+every symbol include/sgc.h declares, and its host-only template code agrees
+with independent checks."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1903_04395_gb300 as sgc
+import sgcgen
+from tests import pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    sgc.build()
+    return sgc.lib()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "sgc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("sgc_graph_create", "sgc_template_create", "sgc_count", "sgc_count_device",
+                     "sgc_graph_destroy", "sgc_template_destroy", "sgc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    for name in _declared_functions():
+        assert hasattr(built, name), name
+    assert set(sgc.SIGNATURES) == set(_declared_functions())
+
+
+def test_version_and_options(built):
+    assert sgc.sgc_version() >= 100
+    o = sgc.sgc_options_init()
+    assert o.precision == sgc.SGC_FP32 and o.root == -1 and o.batch == 0
+
+
+@pytest.mark.parametrize("parent", [sgcgen.path_tree(1), sgcgen.path_tree(2), sgcgen.path_tree(7), sgcgen.star_tree(6),
+                                    sgcgen.spider_tree([3, 3, 3]), sgcgen.spider_tree([2, 2]),
+                                    sgcgen.spider_tree([1, 2, 3])]
+                         + [sgcgen.pruefer_tree(k, s) for k in (5, 6, 7, 8) for s in (1, 2, 3)])
+def test_template_automorphisms_match_brute_force(built, parent):
+    t = sgc.Template(parent)
+    assert t.automorphisms == pins.aut_brute(parent)
+
+
+def test_template_automorphisms_closed_forms(built):
+    assert sgc.Template(sgcgen.spider_tree([3, 3, 3])).automorphisms == 6
+    for k in range(3, 17):
+        assert sgc.Template(sgcgen.path_tree(k)).automorphisms == 2
+    for k in range(3, 13):
+        assert sgc.Template(sgcgen.star_tree(k)).automorphisms == math.factorial(k - 1)
+
+
+@pytest.mark.parametrize("parent,why", [
+    ([-1, -1, 0], "two roots"),
+    ([1, 2, 0], "no root"),
+    ([-1, 0, 5], "parent out of range"),
+    ([-1, 2, 1], "cycle"),
+    ([-1, 1], "self parent"),
+    ([], "empty"),
+    (list(range(-1, 16)), "k above the maximum"),
+])
+def test_template_rejects_invalid(built, parent, why):
+    with pytest.raises(sgc.SgcError) as ei:
+        sgc.sgc_template_create(len(parent), np.array(parent if parent else [0], dtype=np.int32))
+    assert ei.value.status == sgc.SGC_ERR_INVALID, why
+
+
+def test_null_arguments_rejected(built):
+    L = sgc.lib()
+    assert L.sgc_count(None, None, None, 0, None, None, None) == sgc.SGC_ERR_INVALID
+    assert L.sgc_graph_stats_get(None, None) == sgc.SGC_ERR_INVALID
+    assert L.sgc_template_create(3, None, None) == sgc.SGC_ERR_INVALID
+    sgc.sgc_graph_destroy(None)
+    sgc.sgc_template_destroy(None)
