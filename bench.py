@@ -1,0 +1,405 @@
+"""Benchmark: color-coding tree counting on GB300.
+
+Default workload (one "step" = one pass of the whole counting path over one
+batch of colorings): R-MAT scale 20 (2^20 vertices, edge factor 16,
+a=0.57 b=0.19 c=0.19 d=0.05, seed 1, duplicates and self-loops removed;
+31.4 M stored entries), template = 10-vertex spider (centre with three legs
+of three), k = 10 colors, 8 colorings per step, FP32 count tables with FP64
+final reduction.  FP64 tables are timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sgc|reference]
+
+Under torchrun (N > 1) every rank counts its own colorings on its own GPU
+(colorings are independent: weak scaling, no data-path collective); the
+timed region is bracketed by barriers and the max over ranks is taken.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "colorings/sec and SpMM+eMA HBM GB/s (vs ~8 TB/s) per template; p50/p99 query latency"
+WORKLOADS = {
+    "rmat20-spider10": dict(scale=20, template="spider", legs=[3, 3, 3], k=10, batch=8,
+                            desc="R-MAT scale 20 (edge factor 16, a=.57 b=.19 c=.19, seed 1), 10-vertex spider "
+                                 "(legs 3,3,3), k=10, 8 colorings per step"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["sgc", "reference"], default="sgc")
+    ap.add_argument("--workload", default="rmat20-spider10", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_graph(wl):
+    import sgcgen
+    return sgcgen.rmat(wl["scale"], edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+
+
+def make_template(wl):
+    import sgcgen
+    return sgcgen.spider_tree(wl["legs"])
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1903_04395_gb300", "csrc", "kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    for r in rec.get("kernels", []):
+        if r.get("op") == kernel_name and r.get("kernels_sha") == source_sha():
+            return r.get("dram_bytes_per_pass")
+    return None
+
+
+def oracle_sample(wl, scale, seed):
+    """Oracle (exact CPU DP) on one coloring of the workload's template on R-MAT `scale`; returns seconds."""
+    import oracle
+    import sgcgen
+    rp, ci = sgcgen.rmat(scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    parent = make_template(wl)
+    cols = oracle.colors(seed, len(rp) - 1, wl["k"])
+    t0 = time.perf_counter()
+    oracle.count(rp, ci, parent, cols)
+    return time.perf_counter() - t0, len(rp) - 1, len(ci)
+
+
+def oracle_work(n, nnz, parent, k):
+    """Pruned-DP work of the oracle: sum over steps of nnz*C(k,p) + n*C(k,t)*C(t,p) (Lemma 1)."""
+    import sgcgen  # noqa: F401
+    kids = {i: [] for i in range(len(parent))}
+    root = int(np.where(np.asarray(parent) < 0)[0][0])
+    for i, p in enumerate(parent):
+        if p >= 0:
+            kids[int(p)].append(i)
+    size = {}
+
+    def sub(x):
+        size[x] = 1 + sum(sub(c) for c in kids[x])
+        return size[x]
+    sub(root)
+    work = 0.0
+    for x in range(len(parent)):
+        a = 1
+        for c in reversed(sorted(kids[x])):
+            p = size[c]
+            t = a + p
+            work += nnz * math.comb(k, p) + n * math.comb(k, t) * math.comb(t, p)
+            a = t
+    return work
+
+
+def run_reference(args, wl, rank, world):
+    """The oracle timed on the host cores: each step one coloring of the workload's template on an R-MAT
+    scale-17 sample, scaled to the full workload by the ratio of the oracle's Lemma-1 work."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sample_scale = 17
+    full_n, full_nnz = 1 << wl["scale"], None
+    import sgcgen
+    rp, ci = sgcgen.rmat(sample_scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    full_rp, full_ci = make_graph(wl)
+    full_nnz = len(full_ci)
+    parent = make_template(wl)
+    ratio = oracle_work(full_n, full_nnz, parent, wl["k"]) / oracle_work(len(rp) - 1, len(ci), parent, wl["k"])
+    cols = [oracle.colors(s + 1, len(rp) - 1, wl["k"]) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        oracle.count(rp, ci, parent, cols[s])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.count(rp, ci, parent, cols[args.warmup + s])
+    dt = time.perf_counter() - t0
+    sample_rate = args.steps / dt
+    value = sample_rate / ratio
+    sample = (f"one coloring per step of the same template and k on R-MAT scale {sample_scale} "
+              f"({len(rp) - 1} vertices, {len(ci)} entries); rate scaled by the oracle's Lemma-1 work ratio "
+              f"{ratio:.2f} to the scale-{wl['scale']} workload")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "colorings/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps * ratio,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": config_of(wl, world),
+        "cpu_baseline": {"value": value, "unit": "colorings/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "colorings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def config_of(wl, world):
+    return {"workload": args_workload_name(wl), "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
+            % wl["scale"], "template": "spider legs %s" % (wl["legs"],), "k": wl["k"],
+            "colorings_per_step_per_gpu": wl["batch"], "tables": "fp32 (power-of-two scaled), fp64 final reduction",
+            "parallelism": f"colorings sharded over {world} GPU(s), no collective in the data path",
+            "l2": "inputs larger than L2 (count tables of several GB per step)"}
+
+
+_WL_NAME = {}
+
+
+def args_workload_name(wl):
+    return _WL_NAME.get(id(wl), "rmat20-spider10")
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    _WL_NAME[id(wl)] = args.workload
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    import paper_1903_04395_gb300 as sgc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        sgc.build()
+    if dist:
+        dist.barrier()
+    sgc.lib()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    rp, ci = make_graph(wl)
+    n, nnz = len(rp) - 1, len(ci)
+    parent = make_template(wl)
+    B = wl["batch"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    d_rp = torch.from_numpy(rp).cuda()
+    d_ci = torch.from_numpy(ci).cuda()
+    g = sgc.Graph.from_device(n, nnz, d_rp.data_ptr(), d_ci.data_ptr(), stream=stream.cuda_stream)
+    t = sgc.Template(parent)
+    K, W = args.steps, args.warmup
+    total_steps = W + K
+    # distinct seeds for every (rank, step, coloring)
+    seeds = torch.arange(total_steps * B, dtype=torch.int64, device="cuda") + 1 + rank * 1_000_000
+    out = torch.zeros(total_steps * B, dtype=torch.float64, device="cuda")
+
+    def run_steps(opt, s0, s1):
+        for s in range(s0, s1):
+            sgc.sgc_count_device(g.handle, t.handle, seeds[s * B:].data_ptr(), B, opt, out[s * B:].data_ptr())
+
+    def timed(opt, warm, steps, profile=False, clocks=False):
+        run_steps(opt, 0, warm)
+        torch.cuda.synchronize()
+        if profile:
+            sgc.sgc_profile_enable(g.handle, True)
+        l0 = g.stats()["kernel_launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run_steps(opt, warm, warm + steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        if sampler:
+            sampler.__exit__()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            x = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            ms = float(x.item())
+        launches = g.stats()["kernel_launches"] - l0
+        prof = sgc.sgc_profile_read(g.handle) if profile else None
+        if profile:
+            sgc.sgc_profile_enable(g.handle, False)
+        return ms, launches, prof, (sampler.summary() if sampler else None)
+
+    opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream)
+    ms, launches, prof, clocks = timed(opt32, W, K, profile=True, clocks=True)
+    value = world * K * B / (ms / 1e3)
+    res = {"metric": METRIC, "value": value, "unit": "colorings/s", "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": config_of(wl, world)}
+
+    # roofline of the dominant op, from the CUDA events recorded around every op in the timed region
+    peak, peak_kind = measured_peak()
+    ops = []
+    for e in prof:
+        avg_ms = e["ms"] / max(e["passes"], 1)
+        ops.append({"op": f"{e['name']}(t={e['t']},a={e['a']},p={e['p']})", "kind": e["name"],
+                    "passes": e["passes"], "kernels": e["kernels"], "ms_per_pass": avg_ms,
+                    "alg_bytes_per_pass": e["bytes"], "gbs": e["bytes"] / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0,
+                    "share": e["ms"] / max(sum(x["ms"] for x in prof), 1e-9)})
+    ops.sort(key=lambda o: -o["share"])
+    dom = ops[0]
+    achieved = dom["gbs"]
+    res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "traffic": recorded_traffic(dom["op"]), "kernel": dom["op"],
+                       "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'})"}
+    se = [o for o in ops if o["kind"] in ("spmm", "hist", "gather", "ema", "final", "final_leaf")]
+    se_bytes = sum(o["alg_bytes_per_pass"] * o["passes"] for o in se)
+    se_ms = sum(o["ms_per_pass"] * o["passes"] for o in se)
+    res["spmm_ema_alg_gbs"] = se_bytes / (se_ms * 1e-3) / 1e9 if se_ms else None
+    res["ops"] = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in o.items()} for o in ops]
+    res["gpu_launches"] = launches
+    res["clocks"] = clocks
+    # correctness spot check of the first timed coloring against itself in FP64 is left to the tests
+
+    if not args.no_fp64:
+        opt64 = sgc.sgc_options_init(precision=sgc.SGC_FP64, batch=B, stream=stream.cuda_stream)
+        k64 = max(2, K // 6)
+        ms64, _, _, _ = timed(opt64, 1, k64)
+        res["fp64"] = {"value": world * k64 * B / (ms64 / 1e3), "unit": "colorings/s", "steps": k64,
+                       "ms_per_step": ms64 / k64, "dtype": "f64"}
+
+    if not args.no_e2e:
+        # the user-facing call with host buffers: graph upload from pinned host memory, counting with host
+        # seeds, result read back to the host, graph released - every step
+        h_rp = torch.from_numpy(rp).pin_memory()
+        h_ci = torch.from_numpy(ci).pin_memory()
+        maps_host = np.zeros(B, dtype=np.float64)
+        k_e2e = max(3, K // 6)
+
+        def e2e_step(s):
+            gh = sgc.sgc_graph_create(n, nnz, h_rp.data_ptr(), h_ci.data_ptr(), sgc.SGC_GRAPH_VALIDATE)
+            try:
+                sd = np.arange(B, dtype=np.uint64) + np.uint64(5_000_000 + rank * 100_000 + s * B)
+                sgc.sgc_count(gh, t.handle, sd, sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B),
+                              maps_out=maps_host)
+            finally:
+                sgc.sgc_graph_destroy(gh)
+
+        e2e_step(0)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(k_e2e):
+            e2e_step(s + 1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            x = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            dt = float(x.item())
+        res["e2e"] = {"value": world * k_e2e * B / dt, "unit": "colorings/s", "steps": k_e2e,
+                      "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz + 8 * B, "d2h_bytes_per_step": 8 * B,
+                      "includes": "graph upload + validation + renumbering, counting, read-back, release"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        dt, on, onnz = oracle_sample(wl, wl["scale"], seed=1)
+        res["cpu_baseline"] = {"value": 1.0 / dt, "unit": "colorings/s", "cores": oracle.threads(), "kind": "oracle",
+                               "sample": f"one coloring (seed 1) of the full workload ({on} vertices, {onnz} "
+                                         f"entries), exact unsigned 128-bit counts, {dt:.1f} s"}
+
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -112,6 +112,7 @@ typedef struct sgc_graph_stats {
   int32_t n_heavy;    /* rows whose neighbour list is split across warps in SpMM */
   int32_t n_segments; /* neighbour-list segments of those rows */
   int32_t device;     /* CUDA device ordinal */
+  int64_t kernel_launches; /* kernels enqueued so far by calls on this handle */
 } sgc_graph_stats;
 
 sgc_status sgc_graph_stats_get(const sgc_graph* g, sgc_graph_stats* out);
@@ -179,6 +180,32 @@ sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* 
  */
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
                             int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
+
+/* ------------------------------------------------------------ profiling -- */
+
+/* Device time of one kind of DP op, aggregated over the passes recorded
+ * since profiling was enabled or last read.  Times come from CUDA events
+ * recorded on the launching stream immediately before and after the op. */
+typedef struct sgc_op_profile {
+  int32_t kind;      /* 0 coloring, 1 neighbour color histogram, 2 SpMM, 3 single-term eMA,
+                        4 eMA, 5 final step (single-vertex active child), 6 final step */
+  int32_t t, a, p;   /* sub-template sizes |T_s|, |T_a|, |T_p| */
+  int32_t batch;     /* colorings per pass */
+  int64_t passes;    /* passes recorded */
+  int64_t kernels;   /* kernel launches in those passes */
+  double ms;         /* summed device time */
+  double bytes;      /* algorithmic bytes of one pass: every table read or written once,
+                        CSR read once per column tile */
+  double flops;      /* multiplies + adds of one pass (eMA and final step) */
+} sgc_op_profile;
+
+/* Turn event recording around every op on (1) or off (0); turning it on
+ * discards earlier records.  Adds two event records per op to each pass. */
+sgc_status sgc_profile_enable(const sgc_graph* g, int32_t on);
+
+/* Wait for the recorded events, then copy up to `cap` aggregated entries to
+ * `out` (host) and their number to *n; records are cleared. */
+sgc_status sgc_profile_read(const sgc_graph* g, sgc_op_profile* out, int32_t cap, int32_t* n);
 
 #ifdef __cplusplus
 }

@@ -43,7 +43,7 @@ class sgc_options(ctypes.Structure):
 class sgc_graph_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_active", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("max_degree", ctypes.c_int32), ("n_heavy", ctypes.c_int32), ("n_segments", ctypes.c_int32),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
 
 
 class sgc_plan_info(ctypes.Structure):
@@ -51,6 +51,14 @@ class sgc_plan_info(ctypes.Structure):
                 ("n_ema", ctypes.c_int32), ("batch", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
                 ("est_bytes", ctypes.c_double), ("est_spmm_bytes", ctypes.c_double), ("est_fma", ctypes.c_double)]
 
+
+class sgc_op_profile(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("a", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("passes", ctypes.c_int64), ("kernels", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 3: "gather", 4: "ema", 5: "final_leaf", 6: "final"}
 
 # exported symbols with their ctypes signatures (restype, argtypes)
 _P = ctypes.POINTER
@@ -72,6 +80,8 @@ SIGNATURES = {
     "sgc_count": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, _P(sgc_options),
                                  _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sgc_count_device": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+    "sgc_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "sgc_profile_read": (ctypes.c_int, [_vp, _P(sgc_op_profile), ctypes.c_int32, _P(ctypes.c_int32)]),
 }
 
 _lib = None
@@ -119,8 +129,13 @@ def sgc_version() -> int:
 
 
 def sgc_graph_create(n: int, nnz: int, row_ptr, col_idx, flags: int = SGC_GRAPH_VALIDATE) -> int:
-    rp, rpp = _i32(row_ptr)
-    ci, cip = _i32(col_idx)
+    """row_ptr / col_idx: host arrays, or integer host addresses (e.g. pinned buffers)."""
+    if isinstance(row_ptr, int) and isinstance(col_idx, int):
+        rpp = ctypes.cast(row_ptr, _P(ctypes.c_int32))
+        cip = ctypes.cast(col_idx, _P(ctypes.c_int32))
+    else:
+        rp, rpp = _i32(row_ptr)
+        ci, cip = _i32(col_idx)
     out = _vp()
     _check(lib().sgc_graph_create(n, nnz, rpp, cip, flags, ctypes.byref(out)))
     return out.value
@@ -166,11 +181,11 @@ def sgc_plan_get(g: int, t: int, opt: sgc_options | None = None) -> dict:
     return {f: getattr(info, f) for f, _ in sgc_plan_info._fields_}
 
 
-def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None):
+def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None, maps_out: np.ndarray | None = None):
     """Host-buffer count: returns (estimate, colorful maps per coloring as float64 array)."""
     s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
     n = int(s.size)
-    maps = np.zeros(max(n, 1), dtype=np.float64)
+    maps = maps_out if maps_out is not None and maps_out.size >= max(n, 1) else np.zeros(max(n, 1), dtype=np.float64)
     est = ctypes.c_double(0.0)
     _check(lib().sgc_count(g, t, s.ctypes.data_as(_P(ctypes.c_uint64)) if n else None, n,
                            ctypes.byref(opt) if opt is not None else None, ctypes.byref(est),
@@ -181,6 +196,24 @@ def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None):
 def sgc_count_device(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:
     """Device-buffer count: enqueue on opt.stream (or the graph's stream); no synchronisation."""
     _check(lib().sgc_count_device(g, t, d_seeds, n_iter, ctypes.byref(opt) if opt is not None else None, d_maps))
+
+
+def sgc_profile_enable(g: int, on: bool = True) -> None:
+    _check(lib().sgc_profile_enable(g, 1 if on else 0))
+
+
+def sgc_profile_read(g: int) -> list:
+    """Aggregated per-op device times (CUDA events) since profiling was enabled or last read."""
+    cap = 64
+    buf = (sgc_op_profile * cap)()
+    n = ctypes.c_int32(0)
+    _check(lib().sgc_profile_read(g, buf, cap, ctypes.byref(n)))
+    out = []
+    for i in range(min(n.value, cap)):
+        e = {f: getattr(buf[i], f) for f, _ in sgc_op_profile._fields_}
+        e["name"] = OP_KINDS.get(e["kind"], str(e["kind"]))
+        out.append(e)
+    return out
 
 
 # -------------------------------------------------------------- wrappers --

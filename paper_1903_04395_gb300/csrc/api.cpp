@@ -2,6 +2,7 @@
 // and the host-side driver of sgc_count (batching colorings, workspace,
 // result read-back and the k^k/k! estimator of Section 2.1).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -58,21 +59,35 @@ sgc_status template_tables(const sgc_template* t, const Plan& plan, int device, 
   return SGC_OK;
 }
 
-sgc_status ensure_workspace(const sgc_graph* g, int64_t bytes, cudaStream_t st) {
-  if ((int64_t)g->ws.bytes >= bytes) return SGC_OK;
-  if (g->ws.ptr) {
-    SGC_CUDA_TRY(cudaStreamSynchronize(st));
-    SGC_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(g->ws.ptr);
-    g->ws.ptr = nullptr;
-    g->ws.bytes = 0;
+// One workspace per device, shared by every graph on it.  Passes on
+// different streams are ordered through `last`, an event recorded after the
+// most recent pass that used the workspace.
+struct DevicePool {
+  std::mutex mu;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t last = nullptr;
+};
+
+DevicePool& device_pool(int dev) {
+  static DevicePool pools[64];
+  return pools[dev & 63];
+}
+
+sgc_status ensure_workspace(DevicePool& pool, int64_t bytes) {
+  if ((int64_t)pool.bytes >= bytes) return SGC_OK;
+  if (pool.ptr) {
+    if (pool.last) SGC_CUDA_TRY(cudaEventSynchronize(pool.last));
+    cudaFree(pool.ptr);
+    pool.ptr = nullptr;
+    pool.bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&g->ws.ptr, (size_t)bytes);
+  cudaError_t e = cudaMalloc(&pool.ptr, (size_t)bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(SGC_ERR_OOM, "device workspace of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
   }
-  g->ws.bytes = (size_t)bytes;
+  pool.bytes = (size_t)bytes;
   return SGC_OK;
 }
 
@@ -90,9 +105,18 @@ sgc_options resolve(const sgc_options* opt) {
 }
 
 // Plans for every power-of-two batch up to bmax that fits mem_limit; the
-// root and cut order come from the cost model once and are shared.
+// root and cut order come from the cost model once and are shared.  Cached on
+// the graph per (template, precision, root, bmax).
 sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_options& o, int bmax, int64_t mem_limit,
-                        std::map<int, Plan>* plans, int* bfit) {
+                        std::shared_ptr<PlanSet>* out) {
+  const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
+                          "/" + std::to_string(bmax);
+  for (auto& kv : g->plan_cache)
+    if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
+      *out = kv.second;
+      return SGC_OK;
+    }
+  auto set = std::make_shared<PlanSet>();
   Plan p1;
   sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1);
   if (rc != SGC_OK) return rc;
@@ -100,17 +124,25 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) + " bytes of device workspace, limit " +
                                  std::to_string(mem_limit));
   const int root = p1.root, policy = p1.policy;
-  (*plans)[1] = std::move(p1);
-  int best = 1;
+  set->by_batch[1] = std::move(p1);
+  set->bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
     rc = make_plan(g, t, o.precision, root, policy, b, true, &pb);
     if (rc != SGC_OK) return rc;
     if (pb.ws_bytes > mem_limit) break;
-    (*plans)[b] = std::move(pb);
-    best = b;
+    set->by_batch[b] = std::move(pb);
+    set->bfit = b;
   }
-  *bfit = best;
+  for (auto& kv : g->plan_cache)
+    if (kv.first == key) {
+      kv.second = set;
+      *out = set;
+      return SGC_OK;
+    }
+  if (g->plan_cache.size() >= 64) g->plan_cache.erase(g->plan_cache.begin());
+  g->plan_cache.push_back({key, set});
+  *out = set;
   return SGC_OK;
 }
 
@@ -127,6 +159,8 @@ sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t*
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
   SGC_CUDA_TRY(cudaSetDevice(g->device));
   std::lock_guard<std::mutex> lock(g->mu);
+  DevicePool& pool = device_pool(g->device);
+  std::lock_guard<std::mutex> pool_lock(pool.mu);
   cudaStream_t st = o.stream ? (cudaStream_t)o.stream : g->stream;
   const int k = t->k;
   if (estimate) *estimate = 0.0;
@@ -146,26 +180,28 @@ sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t*
   } else {
     size_t free_b = 0, total_b = 0;
     SGC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const int64_t mem_limit = o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + g->ws.bytes) * 0.9);
+    const int64_t mem_limit = o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + pool.bytes) * 0.9);
     const int bmax = pow2_floor(std::min(32, o.batch > 0 ? o.batch : std::max(1, (int)n_iter)));
-    std::map<int, Plan> plans;
-    int bfit = 1;
-    rc = plan_batches(g, t, o, bmax, mem_limit, &plans, &bfit);
+    std::shared_ptr<PlanSet> plans;
+    rc = plan_batches(g, t, o, bmax, mem_limit, &plans);
     if (rc != SGC_OK) return rc;
-    const Plan& top = plans[bfit];
+    const Plan& top = plans->by_batch.at(plans->bfit);
     const uint32_t* d_tabs = nullptr;
     if ((rc = template_tables(t, top, g->device, &d_tabs)) != SGC_OK) return rc;
-    if ((rc = ensure_workspace(g, top.ws_bytes, st)) != SGC_OK) return rc;
-    char* ws = static_cast<char*>(g->ws.ptr);
+    if ((rc = ensure_workspace(pool, top.ws_bytes)) != SGC_OK) return rc;
+    if (!pool.last) SGC_CUDA_TRY(cudaEventCreateWithFlags(&pool.last, cudaEventDisableTiming));
+    SGC_CUDA_TRY(cudaStreamWaitEvent(st, pool.last, 0));
+    char* ws = static_cast<char*>(pool.ptr);
+    Profiler* prof = g->prof.on ? &g->prof : nullptr;
     for (int32_t i = 0; i < n_iter;) {
-      int b = bfit;
+      int b = plans->bfit;
       while (b > n_iter - i) b /= 2;
-      const Plan& plan = plans[b];
+      const Plan& plan = plans->by_batch.at(b);
       char* d_seeds = ws + plan.bufs[plan.buf_seeds].offset;
       char* d_out = ws + plan.bufs[plan.buf_out].offset;
       SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds + i, sizeof(uint64_t) * b,
                                    device_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      if ((rc = run_pass(g, plan, d_tabs, ws, st)) != SGC_OK) return rc;
+      if ((rc = run_pass(g, plan, d_tabs, ws, st, prof, &g->kernel_launches)) != SGC_OK) return rc;
       if (device_io) {
         SGC_CUDA_TRY(cudaMemcpyAsync(maps_out + i, d_out, sizeof(double) * b, cudaMemcpyDeviceToDevice, st));
       } else {
@@ -173,6 +209,7 @@ sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t*
       }
       i += b;
     }
+    SGC_CUDA_TRY(cudaEventRecord(pool.last, st));
     if (!device_io) SGC_CUDA_TRY(cudaStreamSynchronize(st));
     SGC_CUDA_TRY(cudaGetLastError());
   }
@@ -229,6 +266,8 @@ sgc_status sgc_graph_stats_get(const sgc_graph* g, sgc_graph_stats* out) {
   out->n_heavy = g->n_heavy;
   out->n_segments = g->n_seg;
   out->device = g->device;
+  std::lock_guard<std::mutex> lock(g->mu);
+  out->kernel_launches = g->kernel_launches;
   return SGC_OK;
 }
 
@@ -249,7 +288,9 @@ sgc_status sgc_template_create(int32_t k, const int32_t* parent, sgc_template** 
     }
   }
   if (roots != 1) return fail(SGC_ERR_INVALID, "parent must have exactly one root (-1)");
+  static std::atomic<int64_t> next_uid{1};
   sgc_template* t = new sgc_template();
+  t->uid = next_uid++;
   t->k = k;
   t->parent.assign(parent, parent + k);
   t->adj.assign(k, {});
@@ -326,6 +367,52 @@ sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* 
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds, int32_t n_iter,
                             const sgc_options* opt, double* d_colorful_maps) {
   return count_impl(g, t, d_seeds, n_iter, opt, true, nullptr, d_colorful_maps);
+}
+
+sgc_status sgc_profile_enable(const sgc_graph* g, int32_t on) {
+  if (!g) return fail(SGC_ERR_INVALID, "graph is NULL");
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaSetDevice(g->device);
+  for (auto& pe : g->prof.pending) {
+    cudaEventSynchronize(pe.e1);
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
+  g->prof.pending.clear();
+  g->prof.agg.clear();
+  g->prof.on = on != 0;
+  return SGC_OK;
+}
+
+sgc_status sgc_profile_read(const sgc_graph* g, sgc_op_profile* out, int32_t cap, int32_t* n) {
+  if (!g || !n || (cap > 0 && !out)) return fail(SGC_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lock(g->mu);
+  SGC_CUDA_TRY(cudaSetDevice(g->device));
+  for (auto& pe : g->prof.pending) {
+    SGC_CUDA_TRY(cudaEventSynchronize(pe.e1));
+    float ms = 0.f;
+    SGC_CUDA_TRY(cudaEventElapsedTime(&ms, pe.e0, pe.e1));
+    g->prof.agg[pe.slot].ms += ms;
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
+  g->prof.pending.clear();
+  *n = (int32_t)g->prof.agg.size();
+  for (int32_t i = 0; i < *n && i < cap; ++i) {
+    const OpProfile& a = g->prof.agg[i];
+    out[i].kind = a.kind;
+    out[i].t = a.t;
+    out[i].a = a.a;
+    out[i].p = a.p;
+    out[i].batch = a.batch;
+    out[i].passes = a.launches;
+    out[i].kernels = a.kernels;
+    out[i].ms = a.ms;
+    out[i].bytes = a.bytes;
+    out[i].flops = a.flops;
+  }
+  g->prof.agg.clear();
+  return SGC_OK;
 }
 
 }  // extern "C"

@@ -116,8 +116,10 @@ void destroy_graph(sgc_graph* g) {
   free_dev(g->d_seg_lo);
   free_dev(g->d_seg_hi);
   free_dev(g->d_heavy_seg);
-  if (g->ws.ptr) cudaFree(g->ws.ptr);
-  g->ws.ptr = nullptr;
+  for (auto& pe : g->prof.pending) {
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
 }

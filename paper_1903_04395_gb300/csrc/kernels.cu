@@ -458,29 +458,25 @@ void launch_spmm_n(int nacc, dim3 grid, cudaStream_t st, const sgc_graph* g, con
 }
 
 template <typename T>
-void launch_spmm(const sgc_graph* g, const T* M, int64_t width, T* P, T* scratch, const ScaleState* si,
-                 ScaleState* so, int num_sms, cudaStream_t st) {
-  constexpr int VN = Vec16<T>::n;
-  const int64_t wv = width / VN;
-  int G = 4;
-  while (G < 32 && G < wv) G *= 2;
-  int nacc = 1;
-  while (nacc < 8 && (int64_t)G * nacc < wv) nacc *= 2;
-  const int64_t tiles = (wv + (int64_t)G * nacc - 1) / ((int64_t)G * nacc);
+int launch_spmm(const sgc_graph* g, const T* M, int64_t width, T* P, T* scratch, const ScaleState* si, ScaleState* so,
+                int num_sms, cudaStream_t st) {
+  const SpmmShape sh = spmm_shape(width, (int)sizeof(T));
   const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
-  const int gpb = kBlock / G;
-  dim3 grid((unsigned)grid_for(nitems, gpb, 1 << 30), (unsigned)tiles);
-  switch (G) {
-    case 4: launch_spmm_n<T, 4>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    case 8: launch_spmm_n<T, 8>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    case 16: launch_spmm_n<T, 16>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    default: launch_spmm_n<T, 32>(nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+  const int gpb = kBlock / sh.g;
+  dim3 grid((unsigned)grid_for(nitems, gpb, 1 << 30), (unsigned)sh.tiles);
+  switch (sh.g) {
+    case 4: launch_spmm_n<T, 4>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    case 8: launch_spmm_n<T, 8>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    case 16: launch_spmm_n<T, 16>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
+    default: launch_spmm_n<T, 32>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
   }
   if (g->n_heavy > 0) {
-    k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * wv, kBlock, 16 * num_sms), kBlock, 0, st>>>(
+    constexpr int VN = Vec16<T>::n;
+    k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * (width / VN), kBlock, 16 * num_sms), kBlock, 0, st>>>(
         g->d_heavy_seg, g->n_heavy, scratch, width, P, width, so);
+    return 2;
   }
-  (void)num_sms;
+  return 1;
 }
 
 template <typename T, int R>
@@ -510,8 +506,26 @@ sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const u
   return SGC_OK;
 }
 
+int profile_slot(Profiler* prof, const PlanOp& op, int batch) {
+  for (size_t i = 0; i < prof->agg.size(); ++i) {
+    const OpProfile& a = prof->agg[i];
+    if (a.kind == op.kind && a.t == op.t && a.a == op.a && a.p == op.p && a.batch == batch) return (int)i;
+  }
+  OpProfile a;
+  a.kind = op.kind;
+  a.t = op.t;
+  a.a = op.a;
+  a.p = op.p;
+  a.batch = batch;
+  a.bytes = op.alg_bytes;
+  a.flops = op.alg_flops;
+  prof->agg.push_back(a);
+  return (int)prof->agg.size() - 1;
+}
+
 template <typename T>
-sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t st) {
+sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t st,
+                      Profiler* prof, int64_t* kernels) {
   int dev = 0, num_sms = 0, smem_optin = 0;
   SGC_CUDA_TRY(cudaGetDevice(&dev));
   SGC_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -529,12 +543,23 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
   const bool fp32 = std::is_same<T, float>::value;
 
   if (fp32) SGC_CUDA_TRY(cudaMemsetAsync(states, 0, sizeof(ScaleState) * (size_t)std::max(1, plan.n_states), st));
+  int64_t nk = 0;
   for (const PlanOp& op : plan.ops) {
+    int slot = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int64_t nk0 = nk;
+    if (prof) {
+      slot = profile_slot(prof, op, B);
+      SGC_CUDA_TRY(cudaEventCreate(&e0));
+      SGC_CUDA_TRY(cudaEventCreate(&e1));
+      SGC_CUDA_TRY(cudaEventRecord(e0, st));
+    }
     switch (op.kind) {
       case OP_COLOR:
         k_color<<<grid_for(rows, kBlock, 8 * num_sms), kBlock, 0, st>>>(
             g->d_orig, g->n_act, B, reinterpret_cast<const uint64_t*>(buf(plan.buf_seeds)), plan.k,
             reinterpret_cast<uint8_t*>(buf(plan.buf_colors)));
+        ++nk;
         break;
       case OP_HIST: {
         T* H = reinterpret_cast<T*>(buf(op.out));
@@ -547,19 +572,23 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         k_hist<T><<<grid_for(nitems, kBlock / 32, 1 << 30), kBlock, smem, st>>>(
             g->d_row_ptr, g->d_col_idx, colors, B, plan.k, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi,
             g->n_heavy, g->n_act, H, op.ld_out, hh, S(op.state_out));
-        if (g->n_heavy > 0)
+        ++nk;
+        if (g->n_heavy > 0) {
           k_hist_heavy_out<T><<<grid_for((int64_t)g->n_heavy * B * op.ld_out, kBlock, 8 * num_sms), kBlock, 0, st>>>(
               hh, g->n_heavy, B, plan.k, H, op.ld_out, S(op.state_out));
+          ++nk;
+        }
         break;
       }
       case OP_SPMM:
-        launch_spmm<T>(g, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p * B, reinterpret_cast<T*>(buf(op.out)),
-                       scratch, S(op.state_p), S(op.state_out), num_sms, st);
+        nk += launch_spmm<T>(g, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p * B,
+                             reinterpret_cast<T*>(buf(op.out)), scratch, S(op.state_p), S(op.state_out), num_sms, st);
         break;
       case OP_GATHER:
         k_gather<T><<<grid_for(rows * op.ld_out, kBlock, 16 * num_sms), kBlock, 0, st>>>(
             colors, rows, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, reinterpret_cast<T*>(buf(op.out)),
             op.ld_out, op.cols_out, d_tabs + op.tab_off, S(op.state_p), S(op.state_out));
+        ++nk;
         break;
       case OP_EMA: {
         sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
@@ -567,12 +596,14 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
                                       d_tabs + op.tab_off, rows, S(op.state_a), S(op.state_p), S(op.state_out),
                                       num_sms, smem_cap, st);
         if (rc != SGC_OK) return rc;
+        ++nk;
         break;
       }
       case OP_FINAL_LEAF:
         k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(colors, reinterpret_cast<const T*>(buf(op.in_p)),
                                                               op.ld_p, d_tabs + op.tab_off, rows, B, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
+        nk += 2;
         break;
       case OP_FINAL:
         k_final<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)), op.ld_a,
@@ -580,18 +611,27 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
                                                          (int)op.cols_p, d_tabs + op.tab_off, rows, B, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, S(op.state_a), S(op.state_p), fp32 ? 1 : 0,
                                       outv);
+        nk += 2;
         break;
+    }
+    if (prof) {
+      SGC_CUDA_TRY(cudaEventRecord(e1, st));
+      prof->pending.push_back({slot, e0, e1});
+      prof->agg[slot].launches += 1;
+      prof->agg[slot].kernels += nk - nk0;
     }
   }
   SGC_CUDA_TRY(cudaGetLastError());
+  if (kernels) *kernels += nk;
   return SGC_OK;
 }
 
 }  // namespace
 
-sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t stream) {
-  if (plan.precision == SGC_FP64) return run_pass_t<double>(g, plan, d_tabs, ws, stream);
-  return run_pass_t<float>(g, plan, d_tabs, ws, stream);
+sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t stream,
+                    Profiler* prof, int64_t* kernels) {
+  if (plan.precision == SGC_FP64) return run_pass_t<double>(g, plan, d_tabs, ws, stream, prof, kernels);
+  return run_pass_t<float>(g, plan, d_tabs, ws, stream, prof, kernels);
 }
 
 }  // namespace sgc

@@ -374,6 +374,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   PlanOp color_op{};
   color_op.kind = OP_COLOR;
   color_op.out = P->buf_colors;
+  color_op.alg_bytes = nv * 4 + nv * batch + 8.0 * batch;
   P->ops.push_back(color_op);
   P->est_bytes += nv * 5;
 
@@ -395,6 +396,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       if (Pc.a < 0) {
         op.kind = OP_HIST;
         op.in_p = P->buf_colors;
+        op.alg_bytes = 4 * (nv + 1) + 4 * nnz + nv * batch + (double)elem * nv * batch * (double)op.cols_out;
         double by = nnz * 4 + nnz * 1 + nv * (double)op.cols_out * elem;
         P->est_bytes += by;
         P->est_spmm_bytes += by;
@@ -406,6 +408,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.ld_p = op.ld_out;
         op.state_p = table_state[C.p];
         max_spmm_width = std::max<int64_t>(max_spmm_width, op.ld_out * batch);
+        const SpmmShape sh = spmm_shape(op.ld_out * batch, elem);
+        op.alg_bytes = 4 * (nv + 1 + nnz) * (double)sh.tiles + 2.0 * elem * nv * batch * (double)op.cols_out;
         double by = nnz * 4 + 2.0 * nv * (double)op.cols_out * elem;
         P->est_bytes += by;
         P->est_spmm_bytes += by;
@@ -439,6 +443,13 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       op.kind = A.a < 0 ? OP_FINAL_LEAF : OP_FINAL;
       op.tab_off = build_tabs ? build_table(ci, op.kind, k, A.size, &P->tabs, &tcache) : 0;
       op.out = P->buf_partials;
+      if (A.a < 0) {
+        op.alg_bytes = nv * batch + (double)elem * nv * batch;
+        op.alg_flops = nv * batch;
+      } else {
+        op.alg_bytes = (double)elem * nv * batch * (double)(op.cols_a + op.cols_p);
+        op.alg_flops = 2.0 * nv * batch * (double)op.cols_p;
+      }
       double by = nv * ((A.a < 0 ? 1.0 : (double)op.cols_a) + (A.a < 0 ? 1.0 : (double)op.cols_p)) * elem;
       P->est_bytes += by;
       P->est_fma += A.a < 0 ? 0.0 : nv * (double)op.cols_p;
@@ -451,6 +462,12 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       op.state_out = table_state[c] = n_states++;
       op.out = table_buf[c] = add_buf(P, "T" + std::to_string(c), rows * op.ld_out * elem, idx);
       P->n_tables++;
+      if (A.a < 0) {
+        op.alg_bytes = nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
+      } else {
+        op.alg_bytes = (double)elem * nv * batch * (double)(op.cols_a + op.cols_p + op.cols_out);
+        op.alg_flops = 2.0 * nv * batch * (double)op.cols_out * (double)op.nsplit;
+      }
       double by = nv * ((A.a < 0 ? 0.0 : (double)op.cols_a) + (double)op.cols_p + (double)op.cols_out) * elem;
       double fm = A.a < 0 ? 0.0 : nv * (double)op.cols_out * (double)op.nsplit;
       P->est_bytes += by;

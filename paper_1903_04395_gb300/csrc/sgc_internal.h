@@ -4,6 +4,8 @@
 
 #include <cstdint>
 #include <array>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -41,11 +43,28 @@ struct ColorIndex {
   uint32_t unrank_mask(uint64_t r, int h) const;
 };
 
-// ------------------------------------------------------------------ graph
-struct Arena {
-  void* ptr = nullptr;
-  size_t bytes = 0;
+// ---------------------------------------------------------------- profile
+// Per-op device time measured with CUDA events recorded on the launching
+// stream around every op of every pass while profiling is on.
+struct OpProfile {
+  int kind = 0, t = 0, a = 0, p = 0, batch = 0;
+  int64_t launches = 0;   // passes recorded
+  int64_t kernels = 0;    // kernel launches of those passes
+  double ms = 0, bytes = 0, flops = 0;  // summed time; algorithmic bytes / flops per pass
 };
+
+struct PendingEvent {
+  int slot;
+  cudaEvent_t e0, e1;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<OpProfile> agg;
+  std::vector<PendingEvent> pending;
+};
+
+struct PlanSet;
 
 }  // namespace sgc
 
@@ -67,13 +86,15 @@ struct sgc_graph {
   int32_t* d_seg_hi = nullptr;    // n_seg: one past the last CSR entry
   int32_t* d_heavy_seg = nullptr; // n_heavy + 1: first segment of each heavy row
   cudaStream_t stream = nullptr;
-  // cached workspace, grown on demand, used by one call at a time
-  mutable std::mutex mu;
-  mutable sgc::Arena ws;
+  mutable std::mutex mu;                  // serialises calls on this handle
+  mutable sgc::Profiler prof;
+  mutable int64_t kernel_launches = 0;    // kernels enqueued by calls on this handle
+  mutable std::vector<std::pair<std::string, std::shared_ptr<sgc::PlanSet>>> plan_cache;
   std::vector<int32_t> h_degree_sorted;  // degrees in new numbering (host copy)
 };
 
 struct sgc_template {
+  int64_t uid = 0;   // unique per created template (plan cache key)
   int32_t k = 0;
   std::vector<int32_t> parent;
   std::vector<std::vector<int32_t>> adj;
@@ -115,6 +136,8 @@ struct PlanOp {
   int64_t nsplit = 0;        // binom(t, p)
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
   int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
+  double alg_bytes = 0;      // algorithmic HBM bytes of one pass (tables read / written once)
+  double alg_flops = 0;      // multiply + add count of one pass
 };
 
 struct Plan {
@@ -156,7 +179,32 @@ struct ScaleState {
 
 // Executes one pass of `plan` for plan.batch colorings whose seeds are in
 // the workspace; writes plan.batch doubles (colorful maps) to the out buffer.
+// With a profiler, CUDA events bracket every op.  *kernels counts launches.
 sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws,
-                    cudaStream_t stream);
+                    cudaStream_t stream, Profiler* prof, int64_t* kernels);
+
+// SpMM launch shape for a row of `width` table entries of `elem` bytes:
+// G lanes per row (4..32), NACC 16-byte vectors per lane (1..8), and the
+// number of column tiles (grid.y) needed to cover the row.
+struct SpmmShape {
+  int g = 4, nacc = 1;
+  int64_t tiles = 1;
+};
+inline SpmmShape spmm_shape(int64_t width, int elem) {
+  SpmmShape s;
+  const int64_t wv = width * elem / 16;
+  while (s.g < 32 && s.g < wv) s.g *= 2;
+  while (s.nacc < 8 && (int64_t)s.g * s.nacc < wv) s.nacc *= 2;
+  s.tiles = (wv + (int64_t)s.g * s.nacc - 1) / ((int64_t)s.g * s.nacc);
+  if (s.tiles < 1) s.tiles = 1;
+  return s;
+}
+
+// Plans for the powers of two up to `bfit` colorings per pass (same root and
+// cut order), cached per graph.
+struct PlanSet {
+  std::map<int, Plan> by_batch;
+  int bfit = 1;
+};
 
 }  // namespace sgc
