@@ -337,7 +337,7 @@ def main():
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "traffic": recorded_traffic(dom["op"]), "kernel": dom["op"],
                        "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'})"}
-    se = [o for o in ops if o["kind"] in ("spmm", "hist", "gather", "ema", "final", "final_leaf")]
+    se = [o for o in ops if o["kind"] in ("spmm", "hist", "ema", "final", "final_leaf")]
     se_bytes = sum(o["alg_bytes_per_pass"] * o["passes"] for o in se)
     se_ms = sum(o["ms_per_pass"] * o["passes"] for o in se)
     res["spmm_ema_alg_gbs"] = se_bytes / (se_ms * 1e-3) / 1e9 if se_ms else None

@@ -187,8 +187,8 @@ sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uin
  * since profiling was enabled or last read.  Times come from CUDA events
  * recorded on the launching stream immediately before and after the op. */
 typedef struct sgc_op_profile {
-  int32_t kind;      /* 0 coloring, 1 neighbour color histogram, 2 SpMM, 3 single-term eMA,
-                        4 eMA, 5 final step (single-vertex active child), 6 final step */
+  int32_t kind;      /* 0 coloring, 1 neighbour color histogram, 2 SpMM, 4 eMA,
+                        5 final step (single-vertex active child), 6 final step */
   int32_t t, a, p;   /* sub-template sizes |T_s|, |T_a|, |T_p| */
   int32_t batch;     /* colorings per pass */
   int64_t passes;    /* passes recorded */

@@ -58,7 +58,7 @@ class sgc_op_profile(ctypes.Structure):
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
-OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 3: "gather", 4: "ema", 5: "final_leaf", 6: "final"}
+OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 4: "ema", 5: "final_leaf", 6: "final"}
 
 # exported symbols with their ctypes signatures (restype, argtypes)
 _P = ctypes.POINTER

@@ -35,10 +35,15 @@ int pow2_floor(int x) {
   return p;
 }
 
-// device copy of a plan's index tables, cached per (device, root, policy)
+// device copy of a plan's index tables, cached per (device, content hash, size)
 sgc_status template_tables(const sgc_template* t, const Plan& plan, int device, const uint32_t** out) {
   std::lock_guard<std::mutex> lock(t->mu);
-  std::array<int, 3> key{device, plan.root, plan.policy};
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the table words
+  for (uint32_t w : plan.tabs) {
+    h ^= w;
+    h *= 1099511628211ull;
+  }
+  std::array<uint64_t, 3> key{(uint64_t)device, h, (uint64_t)plan.tabs.size()};
   for (auto& kv : t->tab_cache)
     if (kv.first == key) {
       *out = kv.second;
@@ -332,7 +337,7 @@ sgc_status sgc_template_automorphisms(const sgc_template* t, uint64_t* aut) {
 void sgc_template_destroy(sgc_template* t) {
   if (!t) return;
   for (auto& kv : t->tab_cache) {
-    cudaSetDevice(kv.first[0]);
+    cudaSetDevice((int)kv.first[0]);
     cudaFree(kv.second);
   }
   delete t;

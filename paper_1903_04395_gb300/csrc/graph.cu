@@ -144,6 +144,7 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
   SGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   g->device = dev;
   g->num_sms = sms;
+  SGC_CUDA_TRY(cudaDeviceGetAttribute(&g->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   g->n = n;
   g->nnz = nnz;
   // row_ptr is always checked (host side): everything below indexes with it

@@ -4,12 +4,24 @@
 // an element-wise multiply-add over the color-set splits (eMA, Section 4.5),
 // and at the last step a reduction over vertices.
 //
+// Relative-color tables.  N(v, T_s, C) is zero unless C contains c(v) (the
+// root of T_s sits on v), and P(v, C_p) is only ever read for C_p without
+// c(v) (C_p and the active child's set are disjoint and the latter holds
+// c(v)).  So every row of vertex v is indexed by subsets of the K = k-1
+// colors other than c(v), relabelled 0..K-1 by skipping c(v) and ranked by
+// Eq. 1 over those labels: a sub-template table of size t keeps C(K, t-1)
+// entries (the set minus c(v)), a P table of a passive child of size p keeps
+// C(K, p).  In this form the eMA with a single-vertex active child is the
+// identity, and every eMA and final split table is the same for all
+// vertices (the plain eMA over K colors); only SpMM, which moves counts
+// between vertices of different colors, re-indexes through a table keyed by
+// the two colors.
+//
 // Layout in HBM.  Every table is vertex-major: the row of vertex v holds the
-// `batch` colorings one after the other, each ld entries wide (ld = number of
-// color sets padded to 16 bytes), i.e. element (v, b, I) sits at
-// ((v * batch + b) * ld + I).  SpMM therefore sees one wide row per vertex
-// (batch * ld columns, coalesced 16-byte gathers per neighbour) and the eMA
-// sees n * batch independent rows.  Padding columns are always written as 0.
+// `batch` colorings one after the other, each ld entries wide (ld = row width
+// padded to 16 bytes), i.e. element (v, b, I) sits at ((v * batch + b) * ld + I).
+// SpMM sees one contiguous row per vertex (coalesced neighbour gathers) and
+// the eMA sees n * batch independent rows.  Padding columns are written as 0.
 //
 // FP32 tables carry a power-of-two scale per table (ScaleState): stored value
 // = count * 2^-e.  Producers choose the shift from their inputs' measured
@@ -89,10 +101,11 @@ __global__ void k_color(const int32_t* __restrict__ orig, int64_t n_act, int bat
 }
 
 // --------------------------------------- passive single vertex: histogram --
-// P(v, {c}) = number of neighbours of v with color c: the SpMM of A with the
-// one-hot leaf table N(u, {x}, {c}) = [c(u) = c], never materialised.
-// One warp per work item; items are the segments of heavy rows (counted with
-// integer atomics into hist_heavy) followed by the light rows.
+// P(v, {d}) = number of neighbours of v with color d, for d != c(v), stored at
+// the relative label of d: the SpMM of A with the one-hot leaf table
+// N(u, {x}, {c}) = [c(u) = c], never materialised.  One warp per work item;
+// items are the segments of heavy rows (counted with integer atomics into
+// hist_heavy, by absolute color) followed by the light rows.
 template <typename T>
 __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                        const uint8_t* __restrict__ colors, int batch, int k, int32_t n_seg,
@@ -131,10 +144,12 @@ __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __res
         if (h[i]) atomicAdd(dst + i, h[i]);
     } else {
       T* out = H + (int64_t)row * batch * ldh;
+      const uint8_t* cv = colors + (int64_t)row * batch;
       for (int64_t i = lane; i < batch * ldh; i += 32) {
         const int b = (int)(i / ldh);
-        const int c = (int)(i - b * ldh);
-        const int32_t cnt = c < k ? h[b * k + c] : 0;
+        const int r = (int)(i - b * ldh);
+        int32_t cnt = 0;
+        if (r < k - 1) cnt = h[b * k + r + (r >= cv[b] ? 1 : 0)];
         out[i] = (T)cnt;
         wmax = fmaxf(wmax, (float)cnt);
       }
@@ -148,14 +163,16 @@ __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __res
 }
 
 template <typename T>
-__global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, int32_t n_heavy, int batch, int k,
-                                 T* __restrict__ H, int64_t ldh, ScaleState* st_out) {
+__global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, const uint8_t* __restrict__ colors,
+                                 int32_t n_heavy, int batch, int k, T* __restrict__ H, int64_t ldh,
+                                 ScaleState* st_out) {
   const int64_t total = (int64_t)n_heavy * batch * ldh;
   float m = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t rb = i / ldh;
-    const int c = (int)(i - rb * ldh);
-    const int32_t cnt = c < k ? hist_heavy[rb * k + c] : 0;
+    const int64_t rb = i / ldh;  // row * batch + b
+    const int r = (int)(i - rb * ldh);
+    int32_t cnt = 0;
+    if (r < k - 1) cnt = hist_heavy[rb * k + r + (r >= colors[rb] ? 1 : 0)];
     H[i] = (T)cnt;
     m = fmaxf(m, (float)cnt);
   }
@@ -163,80 +180,103 @@ __global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, int32_t
 }
 
 // -------------------------------------------------------- SpMM P = A * M --
-// G lanes per work item, each lane owning NACC 16-byte column vectors of
-// the current column tile (blockIdx.y).  Items are heavy-row segments
-// (partial sums into `scratch`, reduced by k_spmm_reduce in segment order)
-// followed by the light rows (written straight to P).  Rows are numbered by
-// degree, highest first, so neighbour gathers concentrate on the hot rows.
-template <typename T, int G, int NACC>
+// P(v, S) = sum over neighbours u of N(u, T_p, S), for p-subsets S without c(v).
+// Neighbour u's row holds N(u, T_p, S'' + c(u)) at the relative index j of the
+// (p-1)-subset S''; it contributes to v's entry for S'' + c(u) unless c(v) is
+// in that set (pos_tab[c(v)][c(u)][j] gives the entry or ~0).
+//
+// One warp per row (or heavy-row segment), accumulating in shared memory.
+// Lane l serves coloring b = l mod batch and the entries j = l / batch + L*q
+// (L = 32 / batch lanes per coloring), so its two colors c(v), c(u) are one
+// byte each per neighbour; entries are fetched in chunks of four independent
+// loads before they are added.  Neighbours are added in CSR order (a warp
+// barrier separates them), so the summation order - and the FP32 result - is
+// fixed.  Heavy-row segments write their partial rows to `scratch`;
+// k_spmm_reduce adds them in segment order.
+
+// color of vertex x under coloring b (word = b / 8, shift = 8 * (b % 8)) from
+// the byte-per-coloring color array of `batch` (a power of two) colorings
+__device__ __forceinline__ int lane_color(const uint8_t* __restrict__ colors, int64_t x, int batch, int word,
+                                          int shift) {
+  const uint8_t* p = colors + x * batch;
+  uint64_t w;
+  if (batch >= 8) w = __ldg(reinterpret_cast<const unsigned long long*>(p) + word);
+  else if (batch == 4) w = __ldg(reinterpret_cast<const unsigned int*>(p));
+  else if (batch == 2) w = __ldg(reinterpret_cast<const unsigned short*>(p));
+  else w = __ldg(p);
+  return (int)((w >> shift) & 0xffu);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_spmm(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
-    int32_t n_heavy, int32_t n_act, const T* __restrict__ M, int64_t ld_row, int64_t width,
-    T* __restrict__ P, T* __restrict__ scratch, const ScaleState* st_in, ScaleState* st_out) {
-  using V = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;
-  const int gpb = blockDim.x / G;
-  const int gid = threadIdx.x / G, gl = threadIdx.x % G;
-  const int64_t wv = width / VN;
-  const int64_t ldv = ld_row / VN;
-  const int64_t tile0 = (int64_t)blockIdx.y * G * NACC;
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k,
+    const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ pos_tab, const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = batch * ld_out;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  T* acc_b;  // this lane's coloring
+  const int L = 32 / batch;
+  const int b = lane & (batch - 1), jl = lane / batch;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;  // entries of this lane per neighbour
+  acc_b = acc + b * ld_out;
+  const int64_t ld_in_row = (int64_t)batch * ld_in, ld_out_row = (int64_t)batch * ld_out;
   const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
-  const V* __restrict__ Mv = reinterpret_cast<const V*>(M);
   float m = 0.f;
-  for (int64_t item = blockIdx.x * (int64_t)gpb + gid; item < nitems; item += (int64_t)gridDim.x * gpb) {
-    int32_t lo, hi;
-    V* dst;
-    bool heavy = item < n_seg;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    int32_t row, lo, hi;
+    const bool heavy = item < n_seg;
     if (heavy) {
+      row = seg_row[item];
       lo = seg_lo[item];
       hi = seg_hi[item];
-      dst = reinterpret_cast<V*>(scratch) + item * wv;
     } else {
-      const int32_t row = n_heavy + (int32_t)(item - n_seg);
+      row = n_heavy + (int32_t)(item - n_seg);
       lo = row_ptr[row];
       hi = row_ptr[row + 1];
-      dst = reinterpret_cast<V*>(P) + (int64_t)row * ldv;
     }
-    V acc[NACC];
-#pragma unroll
-    for (int i = 0; i < NACC; ++i) acc[i] = vzero<V>();
-    int32_t e = lo;
-    for (; e + 4 <= hi; e += 4) {
-      const int32_t u0 = __ldg(col_idx + e), u1 = __ldg(col_idx + e + 1);
-      const int32_t u2 = __ldg(col_idx + e + 2), u3 = __ldg(col_idx + e + 3);
-#pragma unroll
-      for (int i = 0; i < NACC; ++i) {
-        const int64_t cv = tile0 + i * G + gl;
-        if (cv < wv) {
-          const V x0 = __ldg(Mv + (int64_t)u0 * ldv + cv);
-          const V x1 = __ldg(Mv + (int64_t)u1 * ldv + cv);
-          const V x2 = __ldg(Mv + (int64_t)u2 * ldv + cv);
-          const V x3 = __ldg(Mv + (int64_t)u3 * ldv + cv);
-          acc[i] = vadd(acc[i], vadd(vadd(x0, x1), vadd(x2, x3)));
-        }
-      }
-    }
-    for (; e < hi; ++e) {
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = lane_color(colors, row, batch, word, shift) * k;
+    __syncwarp();
+    for (int32_t e = lo; e < hi; ++e) {
       const int32_t u = __ldg(col_idx + e);
-#pragma unroll
-      for (int i = 0; i < NACC; ++i) {
-        const int64_t cv = tile0 + i * G + gl;
-        if (cv < wv) acc[i] = vadd(acc[i], __ldg(Mv + (int64_t)u * ldv + cv));
+      const int cu = lane_color(colors, u, batch, word, shift);
+      const uint32_t* pt = pos_tab + (int64_t)(cvk + cu) * w_in + jl;
+      const T* src = Min + (int64_t)u * ld_in_row + (int64_t)b * ld_in + jl;
+      int q = 0;
+      for (; q + 4 <= ns; q += 4) {
+        const uint32_t p0 = __ldg(pt + L * q), p1 = __ldg(pt + L * (q + 1));
+        const uint32_t p2 = __ldg(pt + L * (q + 2)), p3 = __ldg(pt + L * (q + 3));
+        const T x0 = __ldg(src + L * q), x1 = __ldg(src + L * (q + 1));
+        const T x2 = __ldg(src + L * (q + 2)), x3 = __ldg(src + L * (q + 3));
+        if (p0 != 0xFFFFFFFFu) acc_b[p0] += x0;
+        if (p1 != 0xFFFFFFFFu) acc_b[p1] += x1;
+        if (p2 != 0xFFFFFFFFu) acc_b[p2] += x2;
+        if (p3 != 0xFFFFFFFFu) acc_b[p3] += x3;
       }
-    }
-#pragma unroll
-    for (int i = 0; i < NACC; ++i) {
-      const int64_t cv = tile0 + i * G + gl;
-      if (cv < wv) {
-        dst[cv] = acc[i];
-        if (!heavy) m = fmaxf(m, vmax(acc[i]));
+      for (; q < ns; ++q) {
+        const uint32_t p0 = __ldg(pt + L * q);
+        const T x0 = __ldg(src + L * q);
+        if (p0 != 0xFFFFFFFFu) acc_b[p0] += x0;
       }
+      __syncwarp();
     }
+    T* dst = heavy ? scratch + item * ld_out_row : P + (int64_t)row * ld_out_row;
+    for (int i = lane; i < acc_len; i += 32) {
+      const T x = acc[i];
+      dst[i] = x;
+      if (!heavy) m = fmaxf(m, (float)x);
+    }
+    __syncwarp();
   }
   if (std::is_same<T, float>::value) {
     publish_max(st_out, m);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
   }
 }
 
@@ -260,54 +300,25 @@ __global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_h
   if (std::is_same<T, float>::value) publish_max(st_out, m);
 }
 
-// ------------------------------------ eMA with a single-vertex active child --
-// M_s(v, S) = [c(v) in S] * P(v, S \ {c(v)}): the split sum has one term.
-template <typename T>
-__global__ void k_gather(const uint8_t* __restrict__ colors, int64_t rows, const T* __restrict__ P, int64_t ldp,
-                         T* __restrict__ out, int64_t ldt, int64_t ct, const uint32_t* __restrict__ tab,
-                         const ScaleState* st_p, ScaleState* st_out) {
-  float scale = 1.f;
-  int s = 0;
-  if (std::is_same<T, float>::value) {
-    s = shift_for(state_max(st_p));
-    scale = pow2f(-s);
-  }
-  const int64_t total = rows * ldt;
-  float m = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / ldt;
-    const int64_t col = i - row * ldt;
-    T val = T(0);
-    if (col < ct) {
-      const uint32_t j = __ldg(tab + (int64_t)colors[row] * ct + col);
-      if (j != 0xFFFFFFFFu) val = P[row * ldp + j] * (T)scale;
-    }
-    out[i] = val;
-    m = fmaxf(m, (float)val);
-  }
-  if (std::is_same<T, float>::value) {
-    publish_max(st_out, m);
-    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_p->e + s;
-  }
-}
-
 // ------------------------------------------------------- general eMA --
-// M_s(v, S) = sum over the binom(t, p) splits (A, S \ A) of M_a(v, A) * P(v, S \ A).
-// A block stages R consecutive rows of M_a and P in shared memory, transposed
-// (column-major inside the tile, stride R+1) so that lanes of a warp - one
-// row each - read consecutive banks; the split table entry is the same for
-// the lanes that share an output column (broadcast).
-template <typename T, int R>
+// M_s(v, S) = sum over the splits (A, S \ A) of M_a(v, A) * P(v, S \ A).
+// A block stages R consecutive rows of M_a and P in shared memory as
+// [column][row] (row stride R+1), so that lanes - one row each, RPL rows per
+// lane at stride 32 - read consecutive banks.  The split table holds the two
+// shared-memory word offsets of every split (pre-multiplied by R+1); all
+// lanes that share an output column read the same entry (a broadcast).
+template <typename T, int R, int RPL>
 __global__ void __launch_bounds__(kBlock) k_ema(
     const T* __restrict__ Ma, int64_t lda, int ca, const T* __restrict__ P, int64_t ldp, int cp,
-    T* __restrict__ out, int64_t ldt, int ct, const uint32_t* __restrict__ tab, int nsplit, int64_t rows,
+    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int64_t rows,
     const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sA = reinterpret_cast<T*>(sm_raw);
-  T* sP = sA + (int64_t)ca * (R + 1);
-  constexpr int NSUB = 32 / R;
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  constexpr int RS = R + 1;
+  constexpr int LPC = R >= 32 ? 32 : R;  // lanes sharing one output column
+  constexpr int NSUB = 32 / LPC;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int r = lane % R, sub = lane / R;
+  const int r = lane % LPC, sub = lane / LPC;
   float scale = 1.f;
   int s = 0;
   if (std::is_same<T, float>::value) {
@@ -321,35 +332,45 @@ __global__ void __launch_bounds__(kBlock) k_ema(
     __syncthreads();
     for (int i = threadIdx.x; i < R * ca; i += blockDim.x) {
       const int rr = i / ca, c = i - rr * ca;
-      sA[c * (R + 1) + rr] = rr < nr ? Ma[(r0 + rr) * lda + c] : T(0);
+      sm[c * RS + rr] = rr < nr ? Ma[(r0 + rr) * lda + c] : T(0);
     }
     for (int i = threadIdx.x; i < R * cp; i += blockDim.x) {
       const int rr = i / cp, c = i - rr * cp;
-      sP[c * (R + 1) + rr] = rr < nr ? P[(r0 + rr) * ldp + c] : T(0);
+      sm[(ca + c) * RS + rr] = rr < nr ? P[(r0 + rr) * ldp + c] : T(0);
     }
     __syncthreads();
+    const T* base = sm + r;
     for (int S = warp * NSUB + sub; S < ldt; S += nwarp * NSUB) {
-      T acc = T(0);
+      T acc[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) acc[q] = T(0);
       if (S < ct) {
+        const uint2* tp = tab + S;
         int j = 0;
         for (; j + 4 <= nsplit; j += 4) {
-          const uint32_t e0 = __ldg(tab + (int64_t)j * ct + S);
-          const uint32_t e1 = __ldg(tab + (int64_t)(j + 1) * ct + S);
-          const uint32_t e2 = __ldg(tab + (int64_t)(j + 2) * ct + S);
-          const uint32_t e3 = __ldg(tab + (int64_t)(j + 3) * ct + S);
-          acc += sA[(e0 & 0xFFFF) * (R + 1) + r] * sP[(e0 >> 16) * (R + 1) + r];
-          acc += sA[(e1 & 0xFFFF) * (R + 1) + r] * sP[(e1 >> 16) * (R + 1) + r];
-          acc += sA[(e2 & 0xFFFF) * (R + 1) + r] * sP[(e2 >> 16) * (R + 1) + r];
-          acc += sA[(e3 & 0xFFFF) * (R + 1) + r] * sP[(e3 >> 16) * (R + 1) + r];
+          const uint2 e0 = __ldg(tp), e1 = __ldg(tp + ct), e2 = __ldg(tp + 2 * ct), e3 = __ldg(tp + 3 * ct);
+          tp += 4 * (int64_t)ct;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            acc[q] += base[e0.x + 32 * q] * base[e0.y + 32 * q];
+            acc[q] += base[e1.x + 32 * q] * base[e1.y + 32 * q];
+            acc[q] += base[e2.x + 32 * q] * base[e2.y + 32 * q];
+            acc[q] += base[e3.x + 32 * q] * base[e3.y + 32 * q];
+          }
         }
         for (; j < nsplit; ++j) {
-          const uint32_t e0 = __ldg(tab + (int64_t)j * ct + S);
-          acc += sA[(e0 & 0xFFFF) * (R + 1) + r] * sP[(e0 >> 16) * (R + 1) + r];
+          const uint2 e0 = __ldg(tp);
+          tp += ct;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) acc[q] += base[e0.x + 32 * q] * base[e0.y + 32 * q];
         }
-        acc *= (T)scale;
       }
-      if (r < nr) out[(r0 + r) * ldt + S] = acc;
-      m = fmaxf(m, (float)acc);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const T v = S < ct ? acc[q] * (T)scale : T(0);
+        if (r + 32 * q < nr) out[(r0 + r + 32 * q) * ldt + S] = v;
+        m = fmaxf(m, (float)v);
+      }
     }
   }
   if (std::is_same<T, float>::value) {
@@ -359,8 +380,8 @@ __global__ void __launch_bounds__(kBlock) k_ema(
 }
 
 // ----------------------------------------------- last step + vertex sum --
-// maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p), products and sums in
-// FP64.  Warp w of the fixed grid takes rows w, w + W, ... (W a multiple of
+// maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p); each row's products are
+// summed per lane in the table type and the per-vertex totals in FP64.  Warp w of the fixed grid takes rows w, w + W, ... (W a multiple of
 // the batch, so a warp always sees the same coloring); per-block partials per
 // coloring are then summed in block order by k_final_sum: the result does
 // not depend on scheduling.
@@ -374,9 +395,11 @@ __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int6
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   double acc = 0.0;
   for (int64_t row = gw; row < rows; row += W) {
-    double v = 0.0;
-    for (int i = lane; i < cp; i += 32)
-      v += (double)Ma[row * lda + __ldg(tab + i)] * (double)P[row * ldp + i];
+    // the row's dot product in the table type (FP32 path: exact products of
+    // values <= 1 and <= max degree, summed in FP32 per lane), then FP64
+    T part = T(0);
+    for (int i = lane; i < cp; i += 32) part += Ma[row * lda + __ldg(tab + i)] * P[row * ldp + i];
+    double v = (double)part;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     acc += v;
@@ -395,16 +418,16 @@ __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int6
   }
 }
 
-// last step with a single-vertex active child: maps_b = sum_v P(v, [k] \ {c(v)})
+// last step with a single-vertex active child: maps_b = sum_v P(v, all colors but c(v)),
+// the single entry of the relative P row
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_final_leaf(const uint8_t* __restrict__ colors, const T* __restrict__ P,
-                                                       int64_t ldp, const uint32_t* __restrict__ tab, int64_t rows,
-                                                       int batch, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kBlock) k_final_leaf(const T* __restrict__ P, int64_t ldp, int64_t rows, int batch,
+                                                       double* __restrict__ partials) {
   __shared__ double tacc[kBlock];
   const int64_t S = (int64_t)gridDim.x * blockDim.x;  // multiple of batch
   double acc = 0.0;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S)
-    acc += (double)P[row * ldp + __ldg(tab + colors[row])];
+    acc += (double)P[row * ldp];
   tacc[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x < batch) {
@@ -439,70 +462,55 @@ int grid_for(int64_t work, int per_block, int cap) {
   return (int)g;
 }
 
-template <typename T, int G, int NACC>
-void launch_spmm_g(dim3 grid, cudaStream_t st, const sgc_graph* g, const T* M, int64_t ld_row, int64_t width, T* P,
-                   T* scratch, const ScaleState* si, ScaleState* so) {
-  k_spmm<T, G, NACC><<<grid, kBlock, 0, st>>>(g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo,
-                                              g->d_seg_hi, g->n_heavy, g->n_act, M, ld_row, width, P, scratch, si, so);
-}
-
-template <typename T, int G>
-void launch_spmm_n(int nacc, dim3 grid, cudaStream_t st, const sgc_graph* g, const T* M, int64_t ld_row,
-                   int64_t width, T* P, T* scratch, const ScaleState* si, ScaleState* so) {
-  switch (nacc) {
-    case 1: launch_spmm_g<T, G, 1>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
-    case 2: launch_spmm_g<T, G, 2>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
-    case 4: launch_spmm_g<T, G, 4>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
-    default: launch_spmm_g<T, G, 8>(grid, st, g, M, ld_row, width, P, scratch, si, so); break;
-  }
-}
-
 template <typename T>
-int launch_spmm(const sgc_graph* g, const T* M, int64_t width, T* P, T* scratch, const ScaleState* si, ScaleState* so,
-                int num_sms, cudaStream_t st) {
-  const SpmmShape sh = spmm_shape(width, (int)sizeof(T));
+sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, const uint8_t* colors, const T* M,
+                       T* P, T* scratch, const uint32_t* tab, const ScaleState* si, ScaleState* so, int num_sms,
+                       size_t smem_cap, cudaStream_t st, int64_t* nk) {
+  const size_t per_warp = (size_t)batch * op.ld_out * sizeof(T);
+  int wpb = kBlock / 32;
+  while (wpb > 1 && per_warp * wpb > smem_cap) wpb /= 2;
+  if (per_warp * wpb > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "SpMM row does not fit in shared memory");
+  const size_t smem = per_warp * wpb;
+  allow_smem(k_spmm<T>, smem);
   const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
-  const int gpb = kBlock / sh.g;
-  dim3 grid((unsigned)grid_for(nitems, gpb, 1 << 30), (unsigned)sh.tiles);
-  switch (sh.g) {
-    case 4: launch_spmm_n<T, 4>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    case 8: launch_spmm_n<T, 8>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    case 16: launch_spmm_n<T, 16>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-    default: launch_spmm_n<T, 32>(sh.nacc, grid, st, g, M, width, width, P, scratch, si, so); break;
-  }
+  k_spmm<T><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(
+      g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, colors,
+      batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);
+  ++*nk;
   if (g->n_heavy > 0) {
     constexpr int VN = Vec16<T>::n;
+    const int64_t width = (int64_t)batch * op.ld_out;
     k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * (width / VN), kBlock, 16 * num_sms), kBlock, 0, st>>>(
         g->d_heavy_seg, g->n_heavy, scratch, width, P, width, so);
-    return 2;
+    ++*nk;
   }
-  return 1;
+  return SGC_OK;
 }
 
-template <typename T, int R>
+template <typename T, int R, int RPL>
 void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
-                  const ScaleState* sa, const ScaleState* sp, ScaleState* so, int num_sms, cudaStream_t st) {
+                  const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
   const size_t smem = (size_t)(op.cols_a + op.cols_p) * (R + 1) * sizeof(T);
-  allow_smem(k_ema<T, R>, smem);
+  allow_smem(k_ema<T, R, RPL>, smem);
   const int64_t tiles = (rows + R - 1) / R;
-  const int grid = grid_for(tiles, 1, 1 << 30);
-  k_ema<T, R><<<grid, kBlock, smem, st>>>(Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out,
-                                          (int)op.cols_out, tab, (int)op.nsplit, rows, sa, sp, so);
-  (void)num_sms;
+  k_ema<T, R, RPL><<<grid_for(tiles, 1, 1 << 30), kBlock, smem, st>>>(
+      Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out, (int)op.cols_out,
+      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, rows, sa, sp, so);
 }
 
 template <typename T>
 sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
-                      const ScaleState* sa, const ScaleState* sp, ScaleState* so, int num_sms, size_t smem_cap,
-                      cudaStream_t st) {
-  const size_t per = (size_t)(op.cols_a + op.cols_p) * sizeof(T);
-  if (per * 33 <= smem_cap) launch_ema_r<T, 32>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else if (per * 17 <= smem_cap) launch_ema_r<T, 16>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else if (per * 9 <= smem_cap) launch_ema_r<T, 8>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else if (per * 5 <= smem_cap) launch_ema_r<T, 4>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else if (per * 3 <= smem_cap) launch_ema_r<T, 2>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else if (per * 2 <= smem_cap) launch_ema_r<T, 1>(op, Ma, P, out, tab, rows, sa, sp, so, num_sms, st);
-  else return fail(SGC_ERR_UNSUPPORTED, "eMA row does not fit in shared memory");
+                      const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
+  switch (op.ema_rows) {
+    case 64: launch_ema_r<T, 64, 2>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 32: launch_ema_r<T, 32, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 16: launch_ema_r<T, 16, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 8: launch_ema_r<T, 8, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 4: launch_ema_r<T, 4, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 2: launch_ema_r<T, 2, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 1: launch_ema_r<T, 1, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    default: return fail(SGC_ERR_UNSUPPORTED, "eMA row does not fit in shared memory");
+  }
   return SGC_OK;
 }
 
@@ -575,33 +583,29 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         ++nk;
         if (g->n_heavy > 0) {
           k_hist_heavy_out<T><<<grid_for((int64_t)g->n_heavy * B * op.ld_out, kBlock, 8 * num_sms), kBlock, 0, st>>>(
-              hh, g->n_heavy, B, plan.k, H, op.ld_out, S(op.state_out));
+              hh, colors, g->n_heavy, B, plan.k, H, op.ld_out, S(op.state_out));
           ++nk;
         }
         break;
       }
-      case OP_SPMM:
-        nk += launch_spmm<T>(g, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p * B,
-                             reinterpret_cast<T*>(buf(op.out)), scratch, S(op.state_p), S(op.state_out), num_sms, st);
+      case OP_SPMM: {
+        sgc_status rc = launch_spmm<T>(g, op, B, plan.k, colors, reinterpret_cast<const T*>(buf(op.in_p)),
+                                       reinterpret_cast<T*>(buf(op.out)), scratch, d_tabs + op.tab_off,
+                                       S(op.state_p), S(op.state_out), num_sms, smem_cap, st, &nk);
+        if (rc != SGC_OK) return rc;
         break;
-      case OP_GATHER:
-        k_gather<T><<<grid_for(rows * op.ld_out, kBlock, 16 * num_sms), kBlock, 0, st>>>(
-            colors, rows, reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, reinterpret_cast<T*>(buf(op.out)),
-            op.ld_out, op.cols_out, d_tabs + op.tab_off, S(op.state_p), S(op.state_out));
-        ++nk;
-        break;
+      }
       case OP_EMA: {
         sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
                                       reinterpret_cast<const T*>(buf(op.in_p)), reinterpret_cast<T*>(buf(op.out)),
-                                      d_tabs + op.tab_off, rows, S(op.state_a), S(op.state_p), S(op.state_out),
-                                      num_sms, smem_cap, st);
+                                      d_tabs + op.tab_off, rows, S(op.state_a), S(op.state_p), S(op.state_out), st);
         if (rc != SGC_OK) return rc;
         ++nk;
         break;
       }
       case OP_FINAL_LEAF:
-        k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(colors, reinterpret_cast<const T*>(buf(op.in_p)),
-                                                              op.ld_p, d_tabs + op.tab_off, rows, B, partials);
+        k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, rows,
+                                                              B, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
         nk += 2;
         break;

@@ -224,45 +224,91 @@ int64_t pad_ld(int64_t cols, int elem) {
   return (cols + v - 1) / v * v;
 }
 
-struct TabKey {
-  int kind, t, a;
+struct TabKey {  // (kind, t, a, eMA rows) of an index table
+  int kind, t, a, rows;
   bool operator<(const TabKey& o) const {
-    return kind != o.kind ? kind < o.kind : (t != o.t ? t < o.t : a < o.a);
+    if (kind != o.kind) return kind < o.kind;
+    if (t != o.t) return t < o.t;
+    if (a != o.a) return a < o.a;
+    return rows < o.rows;
   }
 };
 
+// eMA block shape: rows staged per block so that both input rows fit in
+// shared memory as [column][row] with row stride rows+1; 64 rows (two per
+// lane) when possible.
+void ema_shape(int64_t ca, int64_t cp, int elem, int smem_cap, int* rows, int* rpl) {
+  const int64_t per = (ca + cp) * elem;
+  const int cands[] = {64, 32, 16, 8, 4, 2, 1};
+  for (int r : cands) {
+    if (per * (r + 1) <= smem_cap) {
+      *rows = r;
+      *rpl = r == 64 ? 2 : 1;
+      return;
+    }
+  }
+  *rows = 0;
+  *rpl = 1;
+}
+
 }  // namespace
 
-static int64_t build_table(const ColorIndex& ci, OpKind kind, int t, int a, std::vector<uint32_t>* tabs,
-                           std::map<TabKey, int64_t>* cache) {
-  TabKey key{(int)kind, t, a};
+// Index tables.  All count tables are stored in relative-color form (see
+// make_plan): a row of vertex v is indexed by subsets of the K = k-1 colors
+// other than c(v), relabelled 0..K-1 by skipping c(v), and ranked by Eq. 1
+// over those K labels.  `ci` ranks subsets of k colors, `cr` of K colors.
+static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int a, std::vector<uint32_t>* tabs,
+                           std::map<TabKey, int64_t>* cache, int ema_rows = 0, int64_t ema_ca = 0) {
+  TabKey key{(int)kind, t, a, ema_rows};
   auto it = cache->find(key);
   if (it != cache->end()) return it->second;
-  const int k = ci.k;
+  const int K = k - 1;
   // align each table to 4 words
   while (tabs->size() % 4) tabs->push_back(0);
   int64_t off = (int64_t)tabs->size();
-  if (kind == OP_GATHER) {
-    // [c][S]: rank of S \ {c} among (t-1)-subsets, or ~0 if c is not in S
-    const uint64_t ct = ci.nsets(t);
-    for (int c = 0; c < k; ++c)
-      for (uint64_t s = 0; s < ct; ++s) {
-        uint32_t m = ci.unrank_mask(s, t);
-        tabs->push_back((m >> c & 1u) ? ci.rank_mask(m & ~(1u << c)) : 0xFFFFFFFFu);
-      }
+  if (kind == OP_SPMM) {
+    // [c_v][c_u][j]: a neighbour u of color c_u holds, at index j, the count for the
+    // (p-1)-subset S of the colors other than c_u (relative to c_u).  Its set S + {c_u}
+    // lands at this index of v's row (relative to c_v), or nowhere (~0) when c_v is in
+    // S + {c_u}: v's P row only keeps sets without c(v).
+    const int p = t;
+    const uint64_t w_in = cr.nsets(p - 1);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
+        for (uint64_t j = 0; j < w_in; ++j) {
+          uint32_t out = 0xFFFFFFFFu;
+          if (cu != cv) {
+            const uint32_t rel_u = cr.unrank_mask(j, p - 1);
+            uint32_t abs_set = 1u << cu;
+            for (int x = 0; x < K; ++x)
+              if (rel_u >> x & 1u) abs_set |= 1u << (x < cu ? x : x + 1);
+            if (!(abs_set >> cv & 1u)) {
+              uint32_t rel_v = 0;
+              for (int y = 0; y < k; ++y)
+                if (abs_set >> y & 1u) rel_v |= 1u << (y < cv ? y : y - 1);
+              out = cr.rank_mask(rel_v);
+            }
+          }
+          tabs->push_back(out);
+        }
   } else if (kind == OP_EMA) {
-    // [j][S]: the j-th split (C_a, C_p) of color set S, packed I(C_a) | I(C_p) << 16
-    const uint64_t ct = ci.nsets(t);
-    const int p = t - a;
-    const uint64_t ns = ci.binom[t][p];
-    std::vector<uint32_t> tab(ns * ct);
+    // [j][S]: the j-th split of the (t-1)-subset S of the K relative colors into an
+    // (a-1)-subset A (active child, minus the root's own color) and S \ A (passive
+    // child), stored as two word offsets into the eMA block's shared memory, which
+    // holds the active rows as [I(A)][row] and then the P rows as [I(S \ A)][row],
+    // row stride ema_rows + 1
+    const int tt = t - 1, aa = a - 1;
+    const uint64_t ct = cr.nsets(tt);
+    const uint64_t ns = cr.binom[tt][aa];
+    const uint32_t rs = (uint32_t)ema_rows + 1;
+    std::vector<uint32_t> tab(2 * ns * ct);
     for (uint64_t s = 0; s < ct; ++s) {
-      uint32_t m = ci.unrank_mask(s, t);
+      const uint32_t m = cr.unrank_mask(s, tt);
       uint64_t j = 0;
-      // submasks of m with popcount a, in decreasing numeric order
       for (uint32_t sub = m;; sub = (sub - 1) & m) {
-        if (__builtin_popcount(sub) == a) {
-          tab[j * ct + s] = ci.rank_mask(sub) | (ci.rank_mask(m & ~sub) << 16);
+        if (__builtin_popcount(sub) == aa) {
+          tab[2 * (j * ct + s)] = cr.rank_mask(sub) * rs;
+          tab[2 * (j * ct + s) + 1] = ((uint32_t)ema_ca + cr.rank_mask(m & ~sub)) * rs;
           ++j;
         }
         if (sub == 0) break;
@@ -270,14 +316,11 @@ static int64_t build_table(const ColorIndex& ci, OpKind kind, int t, int a, std:
     }
     tabs->insert(tabs->end(), tab.begin(), tab.end());
   } else if (kind == OP_FINAL) {
-    // [I_p]: rank of the complement of C_p (an a-subset), t = k
+    // [I_p]: rank of the complement (among all K relative colors) of the p-subset I_p,
+    // an (a-1)-subset: the active child's index for the full color set
     const int p = k - a;
-    const uint32_t full = (k == 32) ? 0xFFFFFFFFu : ((1u << k) - 1);
-    for (uint64_t s = 0; s < ci.nsets(p); ++s) tabs->push_back(ci.rank_mask(full & ~ci.unrank_mask(s, p)));
-  } else if (kind == OP_FINAL_LEAF) {
-    // [c]: rank of all colors but c among (k-1)-subsets
-    const uint32_t full = (1u << k) - 1;
-    for (int c = 0; c < k; ++c) tabs->push_back(ci.rank_mask(full & ~(1u << c)));
+    const uint32_t full = (1u << K) - 1;
+    for (uint64_t s = 0; s < cr.nsets(p); ++s) tabs->push_back(cr.rank_mask(full & ~cr.unrank_mask(s, p)));
   }
   (*cache)[key] = off;
   return off;
@@ -336,9 +379,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   Rooted R;
   root_tree(t, root, &R);
   Builder B(R, policy);
-  const int top = B.build(root, 0);
+  B.build(root, 0);
   const int k = t->k;
-  ColorIndex ci(k);
+  const int K = k - 1;
+  ColorIndex cr(K);
 
   P->k = k;
   P->root = root;
@@ -353,6 +397,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   const int64_t rows = P->rows;
   const int elem = P->elem;
   const double nv = (double)g->n_act, nnz = (double)g->nnz;
+  // widths: a table of a sub-template of size t keeps the (t-1)-subsets of the
+  // other colors; P of a passive child of size p keeps its p-subsets
+  auto w_table = [&](int size) { return (int64_t)cr.nsets(size - 1); };
+  auto w_p = [&](int size) { return (int64_t)cr.nsets(size); };
 
   // fixed buffers; lifetimes are stretched to the whole pass below
   P->buf_seeds = add_buf(P, "seeds", 8LL * batch, 0);
@@ -363,6 +411,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
 
   std::vector<int> table_buf(B.cls.size(), -1), pbuf(B.cls.size(), -1);
   std::vector<int> table_state(B.cls.size(), -1), p_state(B.cls.size(), -1);
+  std::vector<int64_t> table_w(B.cls.size(), 0), table_ld(B.cls.size(), 0);
   std::map<TabKey, int64_t> tcache;
   int n_states = 0;
   P->n_spmm = P->n_ema = 0;
@@ -388,7 +437,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
     if (pbuf[C.p] < 0) {
       PlanOp op{};
       op.p = Pc.size;
-      op.cols_out = (int64_t)ci.nsets(Pc.size);
+      op.cols_out = w_p(Pc.size);
       op.ld_out = pad_ld(op.cols_out, elem);
       op.state_out = p_state[C.p] = n_states++;
       const int idx = (int)P->ops.size();
@@ -404,72 +453,78 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       } else {
         op.kind = OP_SPMM;
         op.in_p = table_buf[C.p];
-        op.cols_p = op.cols_out;
-        op.ld_p = op.ld_out;
+        op.cols_p = table_w[C.p];
+        op.ld_p = table_ld[C.p];
         op.state_p = table_state[C.p];
+        op.tab_off = build_tabs ? build_table(cr, k, OP_SPMM, Pc.size, 0, &P->tabs, &tcache) : 0;
         max_spmm_width = std::max<int64_t>(max_spmm_width, op.ld_out * batch);
-        const SpmmShape sh = spmm_shape(op.ld_out * batch, elem);
-        op.alg_bytes = 4 * (nv + 1 + nnz) * (double)sh.tiles + 2.0 * elem * nv * batch * (double)op.cols_out;
-        double by = nnz * 4 + 2.0 * nv * (double)op.cols_out * elem;
+        op.alg_bytes = 4 * (nv + 1 + nnz) + nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
+        double by = nnz * 4 + (double)elem * nv * (double)(op.cols_p + op.cols_out);
         P->est_bytes += by;
         P->est_spmm_bytes += by;
-        P->est_cost += (by + gather_factor * nnz * (double)op.cols_out * elem) / bw;
+        P->est_cost += (by + gather_factor * nnz * (double)op.cols_p * elem) / bw;
         P->n_spmm++;
       }
       use_buf(P, op.in_p, idx);
       P->ops.push_back(op);
     }
     // ---- the combine step
+    const bool final = C.size == k;
+    if (A.a < 0 && !final) {
+      // single-vertex active child: M_s(v, S + c(v)) = P(v, S), the same numbers
+      table_buf[c] = pbuf[C.p];
+      table_state[c] = p_state[C.p];
+      table_w[c] = w_p(Pc.size);
+      table_ld[c] = pad_ld(table_w[c], elem);
+      continue;
+    }
     PlanOp op{};
     op.t = C.size;
     op.a = A.size;
     op.p = Pc.size;
     op.in_p = pbuf[C.p];
     op.state_p = p_state[C.p];
-    op.cols_p = (int64_t)ci.nsets(Pc.size);
+    op.cols_p = w_p(Pc.size);
     op.ld_p = pad_ld(op.cols_p, elem);
-    op.nsplit = (int64_t)ci.binom[C.size][Pc.size];
+    op.nsplit = (int64_t)cr.binom[C.size - 1][Pc.size];
     const int idx = (int)P->ops.size();
     if (A.a >= 0) {
       op.in_a = table_buf[C.a];
       op.state_a = table_state[C.a];
-      op.cols_a = (int64_t)ci.nsets(A.size);
-      op.ld_a = pad_ld(op.cols_a, elem);
-    } else {
-      op.in_a = P->buf_colors;
+      op.cols_a = table_w[C.a];
+      op.ld_a = table_ld[C.a];
     }
-    const bool final = C.size == k;
     if (final) {
       op.kind = A.a < 0 ? OP_FINAL_LEAF : OP_FINAL;
-      op.tab_off = build_tabs ? build_table(ci, op.kind, k, A.size, &P->tabs, &tcache) : 0;
+      op.tab_off = (build_tabs && A.a >= 0) ? build_table(cr, k, OP_FINAL, k, A.size, &P->tabs, &tcache) : 0;
       op.out = P->buf_partials;
       if (A.a < 0) {
-        op.alg_bytes = nv * batch + (double)elem * nv * batch;
+        op.alg_bytes = (double)elem * nv * batch;
         op.alg_flops = nv * batch;
       } else {
         op.alg_bytes = (double)elem * nv * batch * (double)(op.cols_a + op.cols_p);
         op.alg_flops = 2.0 * nv * batch * (double)op.cols_p;
       }
-      double by = nv * ((A.a < 0 ? 1.0 : (double)op.cols_a) + (A.a < 0 ? 1.0 : (double)op.cols_p)) * elem;
+      double by = nv * ((A.a < 0 ? 0.0 : (double)op.cols_a) + (double)op.cols_p) * elem;
       P->est_bytes += by;
       P->est_fma += A.a < 0 ? 0.0 : nv * (double)op.cols_p;
       P->est_cost += by / bw;
     } else {
-      op.kind = A.a < 0 ? OP_GATHER : OP_EMA;
-      op.cols_out = (int64_t)ci.nsets(C.size);
+      op.kind = OP_EMA;
+      op.cols_out = w_table(C.size);
       op.ld_out = pad_ld(op.cols_out, elem);
-      op.tab_off = build_tabs ? build_table(ci, op.kind, C.size, A.size, &P->tabs, &tcache) : 0;
+      ema_shape(op.cols_a, op.cols_p, elem, g->smem_optin > 0 ? g->smem_optin : 227 * 1024, &op.ema_rows, &op.ema_rpl);
+      op.tab_off = build_tabs ? build_table(cr, k, OP_EMA, C.size, A.size, &P->tabs, &tcache, op.ema_rows, op.cols_a)
+                              : 0;
       op.state_out = table_state[c] = n_states++;
       op.out = table_buf[c] = add_buf(P, "T" + std::to_string(c), rows * op.ld_out * elem, idx);
+      table_w[c] = op.cols_out;
+      table_ld[c] = op.ld_out;
       P->n_tables++;
-      if (A.a < 0) {
-        op.alg_bytes = nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
-      } else {
-        op.alg_bytes = (double)elem * nv * batch * (double)(op.cols_a + op.cols_p + op.cols_out);
-        op.alg_flops = 2.0 * nv * batch * (double)op.cols_out * (double)op.nsplit;
-      }
-      double by = nv * ((A.a < 0 ? 0.0 : (double)op.cols_a) + (double)op.cols_p + (double)op.cols_out) * elem;
-      double fm = A.a < 0 ? 0.0 : nv * (double)op.cols_out * (double)op.nsplit;
+      op.alg_bytes = (double)elem * nv * batch * (double)(op.cols_a + op.cols_p + op.cols_out);
+      op.alg_flops = 2.0 * nv * batch * (double)op.cols_out * (double)op.nsplit;
+      double by = (double)elem * nv * (double)(op.cols_a + op.cols_p + op.cols_out);
+      double fm = nv * (double)op.cols_out * (double)op.nsplit;
       P->est_bytes += by;
       P->est_fma += fm;
       P->est_cost += std::max(by / bw, fm / fma_rate);

@@ -71,6 +71,7 @@ struct PlanSet;
 struct sgc_graph {
   int device = 0;
   int num_sms = 0;
+  int smem_optin = 0;     // bytes of shared memory a block may opt into
   int32_t n = 0;          // vertices as given
   int32_t n_act = 0;      // vertices with degree > 0, renumbered by degree (desc)
   int64_t nnz = 0;
@@ -101,7 +102,7 @@ struct sgc_template {
   uint64_t aut = 0;
   // device copies of the plan index tables, keyed by (device, root, policy)
   mutable std::mutex mu;
-  mutable std::vector<std::pair<std::array<int, 3>, uint32_t*>> tab_cache;
+  mutable std::vector<std::pair<std::array<uint64_t, 3>, uint32_t*>> tab_cache;  // (device, hash, words)
 };
 
 namespace sgc {
@@ -111,8 +112,7 @@ enum OpKind : int32_t {
   OP_COLOR = 0,      // colors of every (vertex, coloring)
   OP_HIST = 1,       // P for a single-vertex passive child: neighbour color histogram
   OP_SPMM = 2,       // P = A * M_p
-  OP_GATHER = 3,     // eMA with a single-vertex active child
-  OP_EMA = 4,        // general eMA over the split table
+  OP_EMA = 4,        // eMA over the split table (a single-vertex active child needs none)
   OP_FINAL_LEAF = 5, // last step, single-vertex active child, fused with the vertex sum
   OP_FINAL = 6,      // last step, general, fused with the vertex sum
 };
@@ -134,6 +134,8 @@ struct PlanOp {
   int64_t cols_a = 0, ld_a = 0;
   int64_t cols_p = 0, ld_p = 0;
   int64_t nsplit = 0;        // binom(t, p)
+  int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
+  int ema_rpl = 1;           // eMA: rows per lane
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
   int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
   double alg_bytes = 0;      // algorithmic HBM bytes of one pass (tables read / written once)

@@ -159,8 +159,9 @@ def test_special_cases():
     rp0 = np.zeros(11, dtype=np.int32)
     g0 = sgc.Graph(rp0, np.zeros(0, dtype=np.int32))
     assert sgc.count(g0, sgc.Template(sgcgen.path_tree(3)), [1]).maps.tolist() == [0.0]
-    # n_iter = 0
-    est, maps = sgc.sgc_count(g.handle, sgc.Template(sgcgen.path_tree(3)).handle, [])
+    # n_iter = 0 (keep the template object alive while its handle is in use)
+    t3 = sgc.Template(sgcgen.path_tree(3))
+    est, maps = sgc.sgc_count(g.handle, t3.handle, [])
     assert est == 0.0 and len(maps) == 0
 
 
