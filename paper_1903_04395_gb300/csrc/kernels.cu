@@ -17,11 +17,13 @@
 // between vertices of different colors, re-indexes through a table keyed by
 // the two colors.
 //
-// Layout in HBM.  Every table is vertex-major: the row of vertex v holds the
-// `batch` colorings one after the other, each ld entries wide (ld = row width
-// padded to 16 bytes), i.e. element (v, b, I) sits at ((v * batch + b) * ld + I).
-// SpMM sees one contiguous row per vertex (coalesced neighbour gathers) and
-// the eMA sees n * batch independent rows.  Padding columns are written as 0.
+// Layout in HBM.  Every table is vertex-major with the `batch` colorings
+// interleaved innermost: element (v, I, b) sits at (v * ld + I) * batch + b
+// (ld = row width padded to 16 bytes).  A vertex's row is one contiguous
+// block (one gather per neighbour in SpMM), and the lanes of a warp that
+// serve consecutive colorings, or consecutive (vertex, coloring) rows in the
+// eMA and final step, touch consecutive addresses.  Padding entries are 0.
+// The eMA and the final step see n * batch rows r = v * batch + b.
 //
 // FP32 tables carry a power-of-two scale per table (ScaleState): stored value
 // = count * 2^-e.  Producers choose the shift from their inputs' measured
@@ -146,8 +148,8 @@ __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __res
       T* out = H + (int64_t)row * batch * ldh;
       const uint8_t* cv = colors + (int64_t)row * batch;
       for (int64_t i = lane; i < batch * ldh; i += 32) {
-        const int b = (int)(i / ldh);
-        const int r = (int)(i - b * ldh);
+        const int r = (int)(i / batch);
+        const int b = (int)(i - (int64_t)r * batch);
         int32_t cnt = 0;
         if (r < k - 1) cnt = h[b * k + r + (r >= cv[b] ? 1 : 0)];
         out[i] = (T)cnt;
@@ -169,8 +171,10 @@ __global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, const u
   const int64_t total = (int64_t)n_heavy * batch * ldh;
   float m = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t rb = i / ldh;  // row * batch + b
-    const int r = (int)(i - rb * ldh);
+    const int64_t row = i / (ldh * batch);
+    const int64_t rem = i - row * ldh * batch;
+    const int r = (int)(rem / batch);
+    const int64_t rb = row * batch + (rem - (int64_t)r * batch);  // row * batch + b
     int32_t cnt = 0;
     if (r < k - 1) cnt = hist_heavy[rb * k + r + (r >= colors[rb] ? 1 : 0)];
     H[i] = (T)cnt;
@@ -183,94 +187,197 @@ __global__ void k_hist_heavy_out(const int32_t* __restrict__ hist_heavy, const u
 // P(v, S) = sum over neighbours u of N(u, T_p, S), for p-subsets S without c(v).
 // Neighbour u's row holds N(u, T_p, S'' + c(u)) at the relative index j of the
 // (p-1)-subset S''; it contributes to v's entry for S'' + c(u) unless c(v) is
-// in that set (pos_tab[c(v)][c(u)][j] gives the entry or ~0).
+// in that set.  One warp per row (or heavy-row segment).  Lane l serves
+// coloring b = l mod batch and the entries j = l / batch + L*q (L = 32 /
+// batch lanes per coloring): consecutive lanes read consecutive words of the
+// neighbour's row, and each lane needs one color byte of u per neighbour.
+// Neighbours are accumulated in CSR order (a warp barrier separates them),
+// so the summation order - and the FP32 result - is fixed.  Heavy-row
+// segments write partial rows to `scratch`; k_spmm_reduce adds them in
+// segment order.
 //
-// One warp per row (or heavy-row segment), accumulating in shared memory.
-// Lane l serves coloring b = l mod batch and the entries j = l / batch + L*q
-// (L = 32 / batch lanes per coloring), so its two colors c(v), c(u) are one
-// byte each per neighbour; entries are fetched in chunks of four independent
-// loads before they are added.  Neighbours are added in CSR order (a warp
-// barrier separates them), so the summation order - and the FP32 result - is
-// fixed.  Heavy-row segments write their partial rows to `scratch`;
-// k_spmm_reduce adds them in segment order.
+// Two forms:
+//  * direct (k_spmm): each entry is added at pos_tab[c(v)][c(u)][j] of v's row
+//    (~0: dropped), accumulated in shared memory.
+//  * bucketed (k_spmm_buckets, narrow rows): entries are summed into one
+//    bucket row per neighbour color, Q[c(u)][j], with no lookup and no bank
+//    conflict; once per row, P(v, S) = sum over the p colors c of S of
+//    Q[c][index of S - c relative to c], read through inv_tab[c(v)][S].
 
-// color of vertex x under coloring b (word = b / 8, shift = 8 * (b % 8)) from
-// the byte-per-coloring color array of `batch` (a power of two) colorings
-__device__ __forceinline__ int lane_color(const uint8_t* __restrict__ colors, int64_t x, int batch, int word,
-                                          int shift) {
-  const uint8_t* p = colors + x * batch;
-  uint64_t w;
-  if (batch >= 8) w = __ldg(reinterpret_cast<const unsigned long long*>(p) + word);
-  else if (batch == 4) w = __ldg(reinterpret_cast<const unsigned int*>(p));
-  else if (batch == 2) w = __ldg(reinterpret_cast<const unsigned short*>(p));
-  else w = __ldg(p);
-  return (int)((w >> shift) & 0xffu);
+struct SpmmItem {
+  int32_t row, lo, hi;
+  bool heavy;
+};
+
+__device__ __forceinline__ SpmmItem spmm_item(int64_t item, int32_t n_seg, const int32_t* __restrict__ seg_row,
+                                              const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+                                              int32_t n_heavy, const int32_t* __restrict__ row_ptr) {
+  SpmmItem it;
+  it.heavy = item < n_seg;
+  if (it.heavy) {
+    it.row = seg_row[item];
+    it.lo = seg_lo[item];
+    it.hi = seg_hi[item];
+  } else {
+    it.row = n_heavy + (int32_t)(item - n_seg);
+    it.lo = row_ptr[it.row];
+    it.hi = row_ptr[it.row + 1];
+  }
+  return it;
 }
 
-template <typename T>
+// color word of vertex x that holds coloring b's byte (8 colorings per word)
+__device__ __forceinline__ uint64_t color_word(const uint8_t* __restrict__ colors, int64_t x, int batch, int word) {
+  const uint8_t* p = colors + x * batch;
+  if (batch >= 8) return __ldg(reinterpret_cast<const unsigned long long*>(p) + word);
+  if (batch == 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
+  if (batch == 2) return __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __ldg(p);
+}
+
+// One warp per row; see the comment above for the lane mapping and the two
+// forms.  NSMAX > 0: the lane's entries per neighbour (at most NSMAX) live in
+// registers and the neighbour loop is software-pipelined - neighbour ids are
+// fetched 32 at a time and shuffled, and the next neighbour's color word and
+// row entries are loaded while the current one is added.  NSMAX = 0: plain
+// loop for wide rows.
+template <typename T, bool BUCKETS, int NSMAX>
 __global__ void __launch_bounds__(kBlock) k_spmm(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
-    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k,
-    const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch,
-    const uint32_t* __restrict__ pos_tab, const ScaleState* st_in, ScaleState* st_out) {
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k, int p,
+    const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int w_out, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ tab_g, int tab_words_smem, const ScaleState* st_in, ScaleState* st_out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int acc_len = batch * ld_out;
+  // direct: accumulators [ld_out][batch]; bucketed: buckets [k][w_in][batch]
+  const int acc_len = BUCKETS ? k * w_in * batch : ld_out * batch;
   T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
-  T* acc_b;  // this lane's coloring
+  // a small index table is staged once per block after the accumulators
+  const uint32_t* tab = tab_g;
+  if (tab_words_smem > 0) {
+    uint32_t* st = reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(sm_raw) + (int64_t)wpb * acc_len);
+    for (int i = threadIdx.x; i < tab_words_smem; i += blockDim.x) st[i] = __ldg(tab_g + i);
+    __syncthreads();
+    tab = st;
+  }
   const int L = 32 / batch;
   const int b = lane & (batch - 1), jl = lane / batch;
   const int word = b >> 3, shift = (b & 7) * 8;
   const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;  // entries of this lane per neighbour
-  acc_b = acc + b * ld_out;
   const int64_t ld_in_row = (int64_t)batch * ld_in, ld_out_row = (int64_t)batch * ld_out;
+  const int step = L * batch;  // distance between a lane's consecutive entries
   const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
   float m = 0.f;
   for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
-    int32_t row, lo, hi;
-    const bool heavy = item < n_seg;
-    if (heavy) {
-      row = seg_row[item];
-      lo = seg_lo[item];
-      hi = seg_hi[item];
-    } else {
-      row = n_heavy + (int32_t)(item - n_seg);
-      lo = row_ptr[row];
-      hi = row_ptr[row + 1];
-    }
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
     for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
-    const int cvk = lane_color(colors, row, batch, word, shift) * k;
+    const int cv = (int)((color_word(colors, it.row, batch, word) >> shift) & 0xffu);
+    const int cvk = cv * k;
     __syncwarp();
-    for (int32_t e = lo; e < hi; ++e) {
-      const int32_t u = __ldg(col_idx + e);
-      const int cu = lane_color(colors, u, batch, word, shift);
-      const uint32_t* pt = pos_tab + (int64_t)(cvk + cu) * w_in + jl;
-      const T* src = Min + (int64_t)u * ld_in_row + (int64_t)b * ld_in + jl;
-      int q = 0;
-      for (; q + 4 <= ns; q += 4) {
-        const uint32_t p0 = __ldg(pt + L * q), p1 = __ldg(pt + L * (q + 1));
-        const uint32_t p2 = __ldg(pt + L * (q + 2)), p3 = __ldg(pt + L * (q + 3));
-        const T x0 = __ldg(src + L * q), x1 = __ldg(src + L * (q + 1));
-        const T x2 = __ldg(src + L * (q + 2)), x3 = __ldg(src + L * (q + 3));
-        if (p0 != 0xFFFFFFFFu) acc_b[p0] += x0;
-        if (p1 != 0xFFFFFFFFu) acc_b[p1] += x1;
-        if (p2 != 0xFFFFFFFFu) acc_b[p2] += x2;
-        if (p3 != 0xFFFFFFFFu) acc_b[p3] += x3;
+    if (NSMAX > 0) {
+      constexpr int NU = NSMAX > 0 ? NSMAX : 1;
+      for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+        const int cnt = min(32, it.hi - e0);
+        const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+        int32_t u = __shfl_sync(0xffffffffu, u_lane, 0);
+        uint64_t cw = color_word(colors, u, batch, word);
+        T x[NU];
+        {
+          const T* src = Min + (int64_t)u * ld_in_row + (int64_t)jl * batch + b;
+#pragma unroll
+          for (int q = 0; q < NU; ++q) x[q] = q < ns ? __ldg(src + (int64_t)step * q) : T(0);
+        }
+        for (int t = 0; t < cnt; ++t) {
+          int32_t un = 0;
+          uint64_t cwn = 0;
+          T xn[NU];
+          if (t + 1 < cnt) {  // prefetch the next neighbour
+            un = __shfl_sync(0xffffffffu, u_lane, t + 1);
+            cwn = color_word(colors, un, batch, word);
+            const T* src = Min + (int64_t)un * ld_in_row + (int64_t)jl * batch + b;
+#pragma unroll
+            for (int q = 0; q < NU; ++q) xn[q] = q < ns ? __ldg(src + (int64_t)step * q) : T(0);
+          }
+          const int cu = (int)((cw >> shift) & 0xffu);
+          if (BUCKETS) {
+            if (cu != cv) {  // a neighbour of v's own color never contributes
+              T* qrow = acc + (cu * w_in + jl) * batch + b;
+#pragma unroll
+              for (int q = 0; q < NU; ++q)
+                if (q < ns) qrow[step * q] += x[q];
+            }
+          } else {
+            const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+            uint32_t pos[NU];
+#pragma unroll
+            for (int q = 0; q < NU; ++q) pos[q] = q < ns ? pt[L * q] : 0xFFFFFFFFu;
+#pragma unroll
+            for (int q = 0; q < NU; ++q)
+              if (pos[q] != 0xFFFFFFFFu) acc[pos[q] * batch + b] += x[q];
+          }
+          __syncwarp();
+          cw = cwn;
+#pragma unroll
+          for (int q = 0; q < NU; ++q) x[q] = xn[q];
+        }
       }
-      for (; q < ns; ++q) {
-        const uint32_t p0 = __ldg(pt + L * q);
-        const T x0 = __ldg(src + L * q);
-        if (p0 != 0xFFFFFFFFu) acc_b[p0] += x0;
+    } else {
+      for (int32_t e = it.lo; e < it.hi; ++e) {
+        const int32_t u = __ldg(col_idx + e);
+        const int cu = (int)((color_word(colors, u, batch, word) >> shift) & 0xffu);
+        const T* src = Min + (int64_t)u * ld_in_row + (int64_t)jl * batch + b;
+        if (BUCKETS) {
+          if (cu != cv) {
+            T* qrow = acc + (cu * w_in + jl) * batch + b;
+            for (int q = 0; q < ns; ++q) qrow[step * q] += __ldg(src + (int64_t)step * q);
+          }
+        } else {
+          const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+          int q = 0;
+          for (; q + 4 <= ns; q += 4) {
+            const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)];
+            const uint32_t p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
+            const T x0 = __ldg(src + (int64_t)step * q), x1 = __ldg(src + (int64_t)step * (q + 1));
+            const T x2 = __ldg(src + (int64_t)step * (q + 2)), x3 = __ldg(src + (int64_t)step * (q + 3));
+            if (p0 != 0xFFFFFFFFu) acc[p0 * batch + b] += x0;
+            if (p1 != 0xFFFFFFFFu) acc[p1 * batch + b] += x1;
+            if (p2 != 0xFFFFFFFFu) acc[p2 * batch + b] += x2;
+            if (p3 != 0xFFFFFFFFu) acc[p3 * batch + b] += x3;
+          }
+          for (; q < ns; ++q) {
+            const uint32_t p0 = pt[L * q];
+            const T x0 = __ldg(src + (int64_t)step * q);
+            if (p0 != 0xFFFFFFFFu) acc[p0 * batch + b] += x0;
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
-    T* dst = heavy ? scratch + item * ld_out_row : P + (int64_t)row * ld_out_row;
-    for (int i = lane; i < acc_len; i += 32) {
-      const T x = acc[i];
-      dst[i] = x;
-      if (!heavy) m = fmaxf(m, (float)x);
+    T* dst = it.heavy ? scratch + item * ld_out_row : P + (int64_t)it.row * ld_out_row;
+    if (BUCKETS) {
+      // resolve: P(v, S) = sum over the colors c of S of Q[c][index of S - c relative to c]
+      for (int i = lane; i < ld_out * batch; i += 32) {
+        const int S = i / batch, bb = i - S * batch;
+        T val = T(0);
+        if (S < w_out) {
+          const int cvb = (int)((color_word(colors, it.row, batch, bb >> 3) >> ((bb & 7) * 8)) & 0xffu);
+          const uint32_t* ent = tab + ((int64_t)cvb * w_out + S) * p;
+          for (int t = 0; t < p; ++t) {
+            const uint32_t e = ent[t];
+            val += acc[((int)(e & 0xffu) * w_in + (int)(e >> 8)) * batch + bb];
+          }
+        }
+        dst[i] = val;
+        if (!it.heavy) m = fmaxf(m, (float)val);
+      }
+    } else {
+      for (int i = lane; i < acc_len; i += 32) {
+        const T x = acc[i];
+        dst[i] = x;
+        if (!it.heavy) m = fmaxf(m, (float)x);
+      }
     }
     __syncwarp();
   }
@@ -310,8 +417,10 @@ __global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_h
 template <typename T, int R, int RPL>
 __global__ void __launch_bounds__(kBlock) k_ema(
     const T* __restrict__ Ma, int64_t lda, int ca, const T* __restrict__ P, int64_t ldp, int cp,
-    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int64_t rows,
+    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int64_t rows, int lb,
     const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+  // element (row r, column c) of a table with row width ld: (r >> lb) * ld * batch + c * batch + (r & bmask)
+  const int64_t bmask = (1 << lb) - 1;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   constexpr int RS = R + 1;
@@ -331,12 +440,14 @@ __global__ void __launch_bounds__(kBlock) k_ema(
     const int nr = (int)(rows - r0 < R ? rows - r0 : R);
     __syncthreads();
     for (int i = threadIdx.x; i < R * ca; i += blockDim.x) {
-      const int rr = i / ca, c = i - rr * ca;
-      sm[c * RS + rr] = rr < nr ? Ma[(r0 + rr) * lda + c] : T(0);
+      const int c = i / R, rr = i - c * R;
+      const int64_t r = r0 + rr;
+      sm[c * RS + rr] = rr < nr ? Ma[(((r >> lb) * lda + c) << lb) + (r & bmask)] : T(0);
     }
     for (int i = threadIdx.x; i < R * cp; i += blockDim.x) {
-      const int rr = i / cp, c = i - rr * cp;
-      sm[(ca + c) * RS + rr] = rr < nr ? P[(r0 + rr) * ldp + c] : T(0);
+      const int c = i / R, rr = i - c * R;
+      const int64_t r = r0 + rr;
+      sm[(ca + c) * RS + rr] = rr < nr ? P[(((r >> lb) * ldp + c) << lb) + (r & bmask)] : T(0);
     }
     __syncthreads();
     const T* base = sm + r;
@@ -368,7 +479,8 @@ __global__ void __launch_bounds__(kBlock) k_ema(
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         const T v = S < ct ? acc[q] * (T)scale : T(0);
-        if (r + 32 * q < nr) out[(r0 + r + 32 * q) * ldt + S] = v;
+        const int64_t rq = r0 + r + 32 * q;
+        if (r + 32 * q < nr) out[(((rq >> lb) * ldt + S) << lb) + (rq & bmask)] = v;
         m = fmaxf(m, (float)v);
       }
     }
@@ -380,40 +492,34 @@ __global__ void __launch_bounds__(kBlock) k_ema(
 }
 
 // ----------------------------------------------- last step + vertex sum --
-// maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p); each row's products are
-// summed per lane in the table type and the per-vertex totals in FP64.  Warp w of the fixed grid takes rows w, w + W, ... (W a multiple of
-// the batch, so a warp always sees the same coloring); per-block partials per
-// coloring are then summed in block order by k_final_sum: the result does
-// not depend on scheduling.
+// maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p).  One thread per row
+// r = v * batch + b, rows r, r + S, ... with S (the grid's thread count) a
+// multiple of the batch, so a thread always serves the same coloring.  A row's
+// products are summed in the table type (exact for FP64 integers; in FP32
+// the products of values <= 1 and <= max degree cannot overflow) and the
+// per-vertex totals in FP64; per-block partials per coloring are summed in
+// block order by k_final_sum, so the result does not depend on scheduling.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int64_t lda, const T* __restrict__ P,
                                                   int64_t ldp, int cp, const uint32_t* __restrict__ tab,
-                                                  int64_t rows, int batch, double* __restrict__ partials) {
-  __shared__ double wacc[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+                                                  int64_t rows, int lb, double* __restrict__ partials) {
+  __shared__ double tacc[kBlock];
+  const int batch = 1 << lb;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
-  for (int64_t row = gw; row < rows; row += W) {
-    // the row's dot product in the table type (FP32 path: exact products of
-    // values <= 1 and <= max degree, summed in FP32 per lane), then FP64
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S) {
+    const int64_t v = row >> lb, b = row & (batch - 1);
+    const T* a = Ma + (v * lda << lb) + b;
+    const T* pp = P + (v * ldp << lb) + b;
     T part = T(0);
-    for (int i = lane; i < cp; i += 32) part += Ma[row * lda + __ldg(tab + i)] * P[row * ldp + i];
-    double v = (double)part;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc += v;
+    for (int i = 0; i < cp; ++i) part += a[(int64_t)__ldg(tab + i) << lb] * pp[(int64_t)i << lb];
+    acc += (double)part;
   }
-  if (lane == 0) wacc[warp] = acc;
+  tacc[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x < batch) {
-    // warps of this block with coloring b are those with (gw mod batch) == b
     double s = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; ++w) {
-      const int64_t g = (int64_t)blockIdx.x * nw + w;
-      if ((int)(g % batch) == (int)threadIdx.x) s += wacc[w];
-    }
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += batch) s += tacc[i];
     partials[(int64_t)blockIdx.x * batch + threadIdx.x] = s;
   }
 }
@@ -421,13 +527,14 @@ __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int6
 // last step with a single-vertex active child: maps_b = sum_v P(v, all colors but c(v)),
 // the single entry of the relative P row
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_final_leaf(const T* __restrict__ P, int64_t ldp, int64_t rows, int batch,
+__global__ void __launch_bounds__(kBlock) k_final_leaf(const T* __restrict__ P, int64_t ldp, int64_t rows, int lb,
                                                        double* __restrict__ partials) {
   __shared__ double tacc[kBlock];
+  const int batch = 1 << lb;
   const int64_t S = (int64_t)gridDim.x * blockDim.x;  // multiple of batch
   double acc = 0.0;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S)
-    acc += (double)P[row * ldp];
+    acc += (double)P[((row >> lb) * ldp << lb) + (row & (batch - 1))];
   tacc[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x < batch) {
@@ -462,20 +569,49 @@ int grid_for(int64_t work, int per_block, int cap) {
   return (int)g;
 }
 
+template <typename T, bool BUCKETS, int NSMAX>
+void launch_spmm_k(const sgc_graph* g, const PlanOp& op, int batch, int k, const uint8_t* colors, const T* M, T* P,
+                   T* scratch, const uint32_t* tab, int tab_smem, const ScaleState* si, ScaleState* so, int wpb,
+                   size_t smem, cudaStream_t st) {
+  allow_smem(k_spmm<T, BUCKETS, NSMAX>, smem);
+  const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+  k_spmm<T, BUCKETS, NSMAX><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(
+      g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, colors,
+      batch, k, op.p, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab, tab_smem,
+      si, so);
+}
+
+// Launch shape of the SpMM: the direct form keeps a plain loop (few registers,
+// high occupancy); the bucketed form (small buckets) uses the pipelined loop.
 template <typename T>
 sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, const uint8_t* colors, const T* M,
                        T* P, T* scratch, const uint32_t* tab, const ScaleState* si, ScaleState* so, int num_sms,
                        size_t smem_cap, cudaStream_t st, int64_t* nk) {
-  const size_t per_warp = (size_t)batch * op.ld_out * sizeof(T);
+  const size_t per_warp = op.spmm_buckets ? (size_t)spmm_bucket_bytes(batch, k, op.cols_p, (int)sizeof(T))
+                                          : (size_t)batch * op.ld_out * sizeof(T);
+  // the bucketed form's resolve table is staged in shared memory when small;
+  // the direct form reads its position table through L1 (staging it in shared
+  // memory measured slower: bank conflicts on the scattered lookups)
+  const int64_t tab_words = (int64_t)k * op.cols_out * op.p;
+  const int tab_smem = op.spmm_buckets && tab_words * 4 <= 16 * 1024 ? (int)tab_words : 0;
   int wpb = kBlock / 32;
-  while (wpb > 1 && per_warp * wpb > smem_cap) wpb /= 2;
-  if (per_warp * wpb > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "SpMM row does not fit in shared memory");
-  const size_t smem = per_warp * wpb;
-  allow_smem(k_spmm<T>, smem);
-  const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
-  k_spmm<T><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(
-      g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, colors,
-      batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);
+  while (wpb > 1 && per_warp * wpb + (size_t)tab_smem * 4 > smem_cap) wpb /= 2;
+  if (per_warp * wpb + (size_t)tab_smem * 4 > smem_cap)
+    return fail(SGC_ERR_UNSUPPORTED, "SpMM row does not fit in shared memory");
+  const size_t smem = per_warp * wpb + (size_t)tab_smem * 4;
+  if (op.spmm_buckets) {
+    const int64_t per_lane = (op.cols_p + 32 / batch - 1) / (32 / batch);
+    if (per_lane <= 4)
+      launch_spmm_k<T, true, 4>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+    else if (per_lane <= 8)
+      launch_spmm_k<T, true, 8>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+    else if (per_lane <= 16)
+      launch_spmm_k<T, true, 16>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+    else
+      launch_spmm_k<T, true, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+  } else {
+    launch_spmm_k<T, false, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+  }
   ++*nk;
   if (g->n_heavy > 0) {
     constexpr int VN = Vec16<T>::n;
@@ -488,27 +624,27 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
 }
 
 template <typename T, int R, int RPL>
-void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
+void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows, int lb,
                   const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
   const size_t smem = (size_t)(op.cols_a + op.cols_p) * (R + 1) * sizeof(T);
   allow_smem(k_ema<T, R, RPL>, smem);
   const int64_t tiles = (rows + R - 1) / R;
   k_ema<T, R, RPL><<<grid_for(tiles, 1, 1 << 30), kBlock, smem, st>>>(
       Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out, (int)op.cols_out,
-      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, rows, sa, sp, so);
+      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, rows, lb, sa, sp, so);
 }
 
 template <typename T>
-sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows,
+sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows, int lb,
                       const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
   switch (op.ema_rows) {
-    case 64: launch_ema_r<T, 64, 2>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 32: launch_ema_r<T, 32, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 16: launch_ema_r<T, 16, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 8: launch_ema_r<T, 8, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 4: launch_ema_r<T, 4, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 2: launch_ema_r<T, 2, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
-    case 1: launch_ema_r<T, 1, 1>(op, Ma, P, out, tab, rows, sa, sp, so, st); break;
+    case 64: launch_ema_r<T, 64, 2>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 32: launch_ema_r<T, 32, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 16: launch_ema_r<T, 16, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 8: launch_ema_r<T, 8, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 4: launch_ema_r<T, 4, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 2: launch_ema_r<T, 2, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
+    case 1: launch_ema_r<T, 1, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
     default: return fail(SGC_ERR_UNSUPPORTED, "eMA row does not fit in shared memory");
   }
   return SGC_OK;
@@ -549,6 +685,9 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
   double* partials = reinterpret_cast<double*>(buf(plan.buf_partials));
   double* outv = reinterpret_cast<double*>(buf(plan.buf_out));
   const bool fp32 = std::is_same<T, float>::value;
+  int lb = 0;
+  while ((1 << lb) < B) ++lb;
+  if ((1 << lb) != B || B > 32) return fail(SGC_ERR_INTERNAL, "batch must be a power of two <= 32");
 
   if (fp32) SGC_CUDA_TRY(cudaMemsetAsync(states, 0, sizeof(ScaleState) * (size_t)std::max(1, plan.n_states), st));
   int64_t nk = 0;
@@ -598,21 +737,21 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
       case OP_EMA: {
         sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
                                       reinterpret_cast<const T*>(buf(op.in_p)), reinterpret_cast<T*>(buf(op.out)),
-                                      d_tabs + op.tab_off, rows, S(op.state_a), S(op.state_p), S(op.state_out), st);
+                                      d_tabs + op.tab_off, rows, lb, S(op.state_a), S(op.state_p), S(op.state_out), st);
         if (rc != SGC_OK) return rc;
         ++nk;
         break;
       }
       case OP_FINAL_LEAF:
         k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, rows,
-                                                              B, partials);
+                                                              lb, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
         nk += 2;
         break;
       case OP_FINAL:
         k_final<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)), op.ld_a,
                                                          reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
-                                                         (int)op.cols_p, d_tabs + op.tab_off, rows, B, partials);
+                                                         (int)op.cols_p, d_tabs + op.tab_off, rows, lb, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, S(op.state_a), S(op.state_p), fp32 ? 1 : 0,
                                       outv);
         nk += 2;

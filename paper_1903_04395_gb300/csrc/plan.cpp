@@ -291,6 +291,28 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
           }
           tabs->push_back(out);
         }
+  } else if (kind == OP_SPMM + 100) {
+    // bucketed SpMM: [c_v][S][t] for the p-subsets S of v's relative colors and the
+    // t-th (ascending) element of S: its absolute color c | (the index, relative to c,
+    // of S minus that element) << 8.  P(v, S) = sum_t bucket[c_t][j_t], where
+    // bucket[c] sums the rows of v's neighbours of color c.
+    const int p = t;
+    const uint64_t w_out = cr.nsets(p);
+    for (int cv = 0; cv < k; ++cv)
+      for (uint64_t s = 0; s < w_out; ++s) {
+        const uint32_t rel_v = cr.unrank_mask(s, p);
+        uint32_t abs_set = 0;
+        for (int x = 0; x < K; ++x)
+          if (rel_v >> x & 1u) abs_set |= 1u << (x < cv ? x : x + 1);
+        for (int c = 0; c < k; ++c) {
+          if (!(abs_set >> c & 1u)) continue;
+          const uint32_t rest = abs_set & ~(1u << c);
+          uint32_t rel_c = 0;
+          for (int y = 0; y < k; ++y)
+            if (rest >> y & 1u) rel_c |= 1u << (y < c ? y : y - 1);
+          tabs->push_back((uint32_t)c | (cr.rank_mask(rel_c) << 8));
+        }
+      }
   } else if (kind == OP_EMA) {
     // [j][S]: the j-th split of the (t-1)-subset S of the K relative colors into an
     // (a-1)-subset A (active child, minus the root's own color) and S \ A (passive
@@ -456,7 +478,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.cols_p = table_w[C.p];
         op.ld_p = table_ld[C.p];
         op.state_p = table_state[C.p];
-        op.tab_off = build_tabs ? build_table(cr, k, OP_SPMM, Pc.size, 0, &P->tabs, &tcache) : 0;
+        op.spmm_buckets = spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketMaxBytes;
+        op.tab_off = build_tabs ? build_table(cr, k, op.spmm_buckets ? (OpKind)(OP_SPMM + 100) : OP_SPMM, Pc.size,
+                                              0, &P->tabs, &tcache)
+                                : 0;
         max_spmm_width = std::max<int64_t>(max_spmm_width, op.ld_out * batch);
         op.alg_bytes = 4 * (nv + 1 + nnz) + nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
         double by = nnz * 4 + (double)elem * nv * (double)(op.cols_p + op.cols_out);

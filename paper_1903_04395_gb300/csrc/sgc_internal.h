@@ -134,6 +134,7 @@ struct PlanOp {
   int64_t cols_a = 0, ld_a = 0;
   int64_t cols_p = 0, ld_p = 0;
   int64_t nsplit = 0;        // binom(t, p)
+  bool spmm_buckets = false; // SpMM: sum neighbour rows per neighbour color, resolve once per row
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_rpl = 1;           // eMA: rows per lane
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
@@ -185,22 +186,11 @@ struct ScaleState {
 sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws,
                     cudaStream_t stream, Profiler* prof, int64_t* kernels);
 
-// SpMM launch shape for a row of `width` table entries of `elem` bytes:
-// G lanes per row (4..32), NACC 16-byte vectors per lane (1..8), and the
-// number of column tiles (grid.y) needed to cover the row.
-struct SpmmShape {
-  int g = 4, nacc = 1;
-  int64_t tiles = 1;
-};
-inline SpmmShape spmm_shape(int64_t width, int elem) {
-  SpmmShape s;
-  const int64_t wv = width * elem / 16;
-  while (s.g < 32 && s.g < wv) s.g *= 2;
-  while (s.nacc < 8 && (int64_t)s.g * s.nacc < wv) s.nacc *= 2;
-  s.tiles = (wv + (int64_t)s.g * s.nacc - 1) / ((int64_t)s.g * s.nacc);
-  if (s.tiles < 1) s.tiles = 1;
-  return s;
+// Shared memory per warp of the bucketed SpMM form: one bucket row per color.
+inline int64_t spmm_bucket_bytes(int batch, int k, int64_t w_in, int elem) {
+  return (int64_t)batch * k * w_in * elem;
 }
+constexpr int64_t kSpmmBucketMaxBytes = 4 * 1024;  // keeps ~48 warps per SM resident
 
 // Plans for the powers of two up to `bfit` colorings per pass (same root and
 // cut order), cached per graph.
