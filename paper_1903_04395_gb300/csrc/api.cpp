@@ -191,8 +191,14 @@ sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t*
     rc = plan_batches(g, t, o, bmax, mem_limit, &plans);
     if (rc != SGC_OK) return rc;
     const Plan& top = plans->by_batch.at(plans->bfit);
-    const uint32_t* d_tabs = nullptr;
-    if ((rc = template_tables(t, top, g->device, &d_tabs)) != SGC_OK) return rc;
+    // every batch size has its own plan and index tables (the SpMM form can
+    // depend on the batch), each uploaded once and cached by content
+    std::map<int, const uint32_t*> d_tabs_by_batch;
+    for (auto& kv : plans->by_batch) {
+      const uint32_t* d = nullptr;
+      if ((rc = template_tables(t, kv.second, g->device, &d)) != SGC_OK) return rc;
+      d_tabs_by_batch[kv.first] = d;
+    }
     if ((rc = ensure_workspace(pool, top.ws_bytes)) != SGC_OK) return rc;
     if (!pool.last) SGC_CUDA_TRY(cudaEventCreateWithFlags(&pool.last, cudaEventDisableTiming));
     SGC_CUDA_TRY(cudaStreamWaitEvent(st, pool.last, 0));
@@ -206,7 +212,7 @@ sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t*
       char* d_out = ws + plan.bufs[plan.buf_out].offset;
       SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds + i, sizeof(uint64_t) * b,
                                    device_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      if ((rc = run_pass(g, plan, d_tabs, ws, st, prof, &g->kernel_launches)) != SGC_OK) return rc;
+      if ((rc = run_pass(g, plan, d_tabs_by_batch.at(b), ws, st, prof, &g->kernel_launches)) != SGC_OK) return rc;
       if (device_io) {
         SGC_CUDA_TRY(cudaMemcpyAsync(maps_out + i, d_out, sizeof(double) * b, cudaMemcpyDeviceToDevice, st));
       } else {

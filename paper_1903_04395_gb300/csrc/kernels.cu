@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
             for (int q = 0; q < NU; ++q) pos[q] = q < ns ? pt[L * q] : 0xFFFFFFFFu;
 #pragma unroll
             for (int q = 0; q < NU; ++q)
-              if (pos[q] != 0xFFFFFFFFu) acc[pos[q] * batch + b] += x[q];
+              if (pos[q] < (uint32_t)ld_out) acc[pos[q] * batch + b] += x[q];
           }
           __syncwarp();
           cw = cwn;
@@ -341,15 +341,15 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
             const uint32_t p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
             const T x0 = __ldg(src + (int64_t)step * q), x1 = __ldg(src + (int64_t)step * (q + 1));
             const T x2 = __ldg(src + (int64_t)step * (q + 2)), x3 = __ldg(src + (int64_t)step * (q + 3));
-            if (p0 != 0xFFFFFFFFu) acc[p0 * batch + b] += x0;
-            if (p1 != 0xFFFFFFFFu) acc[p1 * batch + b] += x1;
-            if (p2 != 0xFFFFFFFFu) acc[p2 * batch + b] += x2;
-            if (p3 != 0xFFFFFFFFu) acc[p3 * batch + b] += x3;
+            if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += x0;
+            if (p1 < (uint32_t)ld_out) acc[p1 * batch + b] += x1;
+            if (p2 < (uint32_t)ld_out) acc[p2 * batch + b] += x2;
+            if (p3 < (uint32_t)ld_out) acc[p3 * batch + b] += x3;
           }
           for (; q < ns; ++q) {
             const uint32_t p0 = pt[L * q];
             const T x0 = __ldg(src + (int64_t)step * q);
-            if (p0 != 0xFFFFFFFFu) acc[p0 * batch + b] += x0;
+            if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += x0;
           }
         }
         __syncwarp();
@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
           const uint32_t* ent = tab + ((int64_t)cvb * w_out + S) * p;
           for (int t = 0; t < p; ++t) {
             const uint32_t e = ent[t];
-            val += acc[((int)(e & 0xffu) * w_in + (int)(e >> 8)) * batch + bb];
+            const int c = (int)(e & 0xffu), j = (int)(e >> 8);
+            if (c < k && j < w_in) val += acc[(c * w_in + j) * batch + bb];
           }
         }
         dst[i] = val;
@@ -512,7 +513,10 @@ __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int6
     const T* a = Ma + (v * lda << lb) + b;
     const T* pp = P + (v * ldp << lb) + b;
     T part = T(0);
-    for (int i = 0; i < cp; ++i) part += a[(int64_t)__ldg(tab + i) << lb] * pp[(int64_t)i << lb];
+    for (int i = 0; i < cp; ++i) {
+      const uint32_t ia = __ldg(tab + i);
+      if (ia < (uint32_t)lda) part += a[(int64_t)ia << lb] * pp[(int64_t)i << lb];
+    }
     acc += (double)part;
   }
   tacc[threadIdx.x] = acc;

@@ -573,6 +573,37 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   place_buffers(P);
 }
 
+// Every index a table holds must stay inside the buffer the kernels use it on.
+static bool tables_in_range(const Plan& P, int k) {
+  for (const PlanOp& op : P.ops) {
+    if (op.tab_off < 0 || P.tabs.empty()) continue;
+    const uint32_t* t = P.tabs.data() + op.tab_off;
+    const int64_t left = (int64_t)P.tabs.size() - op.tab_off;
+    if (op.kind == OP_SPMM && !op.spmm_buckets) {
+      const int64_t n = (int64_t)k * k * op.cols_p;
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; ++i)
+        if (t[i] != 0xFFFFFFFFu && t[i] >= (uint32_t)op.cols_out) return false;
+    } else if (op.kind == OP_SPMM) {
+      const int64_t n = (int64_t)k * op.cols_out * op.p;
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; ++i)
+        if ((int)(t[i] & 0xffu) >= k || (int64_t)(t[i] >> 8) >= op.cols_p) return false;
+    } else if (op.kind == OP_EMA) {
+      const int64_t n = 2 * op.cols_out * op.nsplit;
+      const uint32_t lim = (uint32_t)((op.cols_a + op.cols_p) * (op.ema_rows + 1));
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; ++i)
+        if (t[i] >= lim) return false;
+    } else if (op.kind == OP_FINAL) {
+      if (op.cols_p > left) return false;
+      for (int64_t i = 0; i < op.cols_p; ++i)
+        if (t[i] >= (uint32_t)op.cols_a) return false;
+    }
+  }
+  return true;
+}
+
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
                      bool build_tabs, Plan* out) {
   if (root >= t->k) return fail(SGC_ERR_INVALID, "options.root is not a template vertex");
@@ -595,6 +626,7 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
     }
   }
   plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out);
+  if (build_tabs && !tables_in_range(*out, t->k)) return fail(SGC_ERR_INTERNAL, "index table out of range");
   return SGC_OK;
 }
 

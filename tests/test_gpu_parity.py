@@ -138,6 +138,17 @@ def test_batching_is_invisible():
                                                                                               rtol=FP32_RTOL)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_passes_with_different_spmm_forms(precision):
+    # 11 colorings run as passes of 8 + 2 + 1; the SpMM form of a step can differ between
+    # batch sizes (bucketed for narrow rows), so each pass must use its own index tables
+    rp, ci = sgcgen.er(3000, 12000, 11)
+    parent = sgcgen.pruefer_tree(7, 5)
+    seeds = list(range(100, 111))
+    want, mx = _oracle_maps(rp, ci, parent, seeds)
+    _check(sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision).maps, want, mx, precision)
+
+
 def test_every_root_gives_the_same_count():
     rp, ci = sgcgen.er(2000, 9000, 3)
     g = sgc.Graph(rp, ci)
