@@ -181,6 +181,27 @@ sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* 
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
                             int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
 
+/*
+ * Counting without any device allocation (the paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc while they count, such as
+ * code whose device memory is owned by another framework's allocator or a
+ * service whose device-memory footprint must stay fixed after start-up).
+ * Same arguments and results as sgc_count_device, but every byte of scratch
+ * - count tables, partial rows and sums, colorings, the plan's index tables -
+ * comes from one static device array of SGC_STATIC_WORKSPACE_BYTES, held by
+ * every GPU that loads the library until the process exits.
+ *   - Requests whose single-coloring scratch exceeds that size fail with
+ *     SGC_ERR_UNSUPPORTED (use sgc_count_device); larger batches are split.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make it before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU race.  Each
+ *     call waits for its own work before returning.
+ *   - The graph and template handles are created beforehand (that allocates).
+ */
+#define SGC_STATIC_WORKSPACE_BYTES (64u << 20)
+sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
+                                   int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
+
 /* ------------------------------------------------------------ profiling -- */
 
 /* Device time of one kind of DP op, aggregated over the passes recorded

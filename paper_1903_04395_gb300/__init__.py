@@ -80,6 +80,7 @@ SIGNATURES = {
     "sgc_count": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, _P(sgc_options),
                                  _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sgc_count_device": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+    "sgc_count_device_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
     "sgc_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "sgc_profile_read": (ctypes.c_int, [_vp, _P(sgc_op_profile), ctypes.c_int32, _P(ctypes.c_int32)]),
 }
@@ -196,6 +197,17 @@ def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None, maps_out: n
 def sgc_count_device(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:
     """Device-buffer count: enqueue on opt.stream (or the graph's stream); no synchronisation."""
     _check(lib().sgc_count_device(g, t, d_seeds, n_iter, ctypes.byref(opt) if opt is not None else None, d_maps))
+
+
+SGC_STATIC_WORKSPACE_BYTES = 64 << 20
+
+
+def sgc_count_device_static(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:
+    """Like sgc_count_device, but with no device allocation: all scratch comes from the library's static
+    device array of SGC_STATIC_WORKSPACE_BYTES (for callers that cannot call cudaMalloc while counting).
+    Waits for its work before returning; calls that overlap on the GPU race on the shared array."""
+    _check(lib().sgc_count_device_static(g, t, d_seeds, n_iter, ctypes.byref(opt) if opt is not None else None,
+                                         d_maps))
 
 
 def sgc_profile_enable(g: int, on: bool = True) -> None:
