@@ -32,6 +32,7 @@
 // tables are unscaled exact integers while below 2^53.
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 
 #include "sgc_internal.h"
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
           const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
           int q = 0;
           for (; q + 4 <= ns; q += 4) {
+            // the gathers do not wait for the positions (memory-level parallelism)
             const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)];
             const uint32_t p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
             const T x0 = __ldg(src + (int64_t)step * q), x1 = __ldg(src + (int64_t)step * (q + 1));
@@ -348,8 +350,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
           }
           for (; q < ns; ++q) {
             const uint32_t p0 = pt[L * q];
-            const T x0 = __ldg(src + (int64_t)step * q);
-            if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += x0;
+            if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += __ldg(src + (int64_t)step * q);
           }
         }
         __syncwarp();
@@ -379,6 +380,73 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
         dst[i] = x;
         if (!it.heavy) m = fmaxf(m, (float)x);
       }
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
+// Direct form with the next neighbour's id and color word fetched one step
+// ahead and all of a neighbour's position and row loads issued together
+// (at most NSMAX per lane, unrolled), so each neighbour costs about one memory
+// latency.  Same results and summation order as k_spmm's direct form.
+template <typename T, int NSMAX>
+__global__ void __launch_bounds__(kBlock) k_spmm_direct_pf(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k,
+    const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ tab, const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = ld_out * batch;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const int L = 32 / batch;
+  const int b = lane & (batch - 1), jl = lane / batch;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int64_t ld_in_row = (int64_t)batch * ld_in, ld_out_row = (int64_t)batch * ld_out;
+  const int step = L * batch;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = (int)((color_word(colors, it.row, batch, word) >> shift) & 0xffu) * k;
+    __syncwarp();
+    int32_t u_n = __ldg(col_idx + it.lo);
+    uint64_t cw_n = color_word(colors, u_n, batch, word);
+    for (int32_t e = it.lo; e < it.hi; ++e) {
+      const int32_t u = u_n;
+      const uint64_t cw = cw_n;
+      if (e + 1 < it.hi) {
+        u_n = __ldg(col_idx + e + 1);
+        cw_n = color_word(colors, u_n, batch, word);
+      }
+      const int cu = (int)((cw >> shift) & 0xffu);
+      const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+      const T* src = Min + (int64_t)u * ld_in_row + (int64_t)jl * batch + b;
+      uint32_t pos[NSMAX];
+      T x[NSMAX];
+#pragma unroll
+      for (int q = 0; q < NSMAX; ++q) {
+        pos[q] = q < ns ? pt[L * q] : 0xFFFFFFFFu;
+        x[q] = q < ns ? __ldg(src + (int64_t)step * q) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < NSMAX; ++q)
+        if (pos[q] < (uint32_t)ld_out) acc[pos[q] * batch + b] += x[q];
+      __syncwarp();
+    }
+    T* dst = it.heavy ? scratch + item * ld_out_row : P + (int64_t)it.row * ld_out_row;
+    for (int i = lane; i < acc_len; i += 32) {
+      const T x = acc[i];
+      dst[i] = x;
+      if (!it.heavy) m = fmaxf(m, (float)x);
     }
     __syncwarp();
   }
@@ -418,8 +486,8 @@ __global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_h
 template <typename T, int R, int RPL>
 __global__ void __launch_bounds__(kBlock) k_ema(
     const T* __restrict__ Ma, int64_t lda, int ca, const T* __restrict__ P, int64_t ldp, int cp,
-    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int64_t rows, int lb,
-    const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int sym, int64_t rows,
+    int lb, const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
   // element (row r, column c) of a table with row width ld: (r >> lb) * ld * batch + c * batch + (r & bmask)
   const int64_t bmask = (1 << lb) - 1;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -429,12 +497,13 @@ __global__ void __launch_bounds__(kBlock) k_ema(
   constexpr int NSUB = 32 / LPC;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int r = lane % LPC, sub = lane / LPC;
-  float scale = 1.f;
+  // the symmetric form sums each unordered split once: the factor 2 is exact
+  float scale = sym ? 2.f : 1.f;
   int s = 0;
   if (std::is_same<T, float>::value) {
-    const float bound = (float)nsplit * state_max(st_a) * state_max(st_p);
+    const float bound = (float)(sym ? 2 * nsplit : nsplit) * state_max(st_a) * state_max(st_p);
     s = shift_for(bound);
-    scale = pow2f(-s);
+    scale *= pow2f(-s);
   }
   float m = 0.f;
   for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
@@ -561,6 +630,17 @@ __global__ void k_final_sum(const double* __restrict__ partials, int nblocks, in
   out[b] = s;
 }
 
+// Direct SpMM variant: 0 = chunked loop (default), 1 = next-neighbour prefetch
+// with all loads of a neighbour in flight (measured equal on R-MAT 20, more
+// registers); SGC_SPMM_DIRECT overrides.
+int spmm_direct_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("SGC_SPMM_DIRECT");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
+
 template <typename KernelT>
 void allow_smem(KernelT kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -614,7 +694,21 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
     else
       launch_spmm_k<T, true, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
   } else {
-    launch_spmm_k<T, false, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+    const int64_t per_lane = (op.cols_p + 32 / batch - 1) / (32 / batch);
+    const int variant = spmm_direct_variant();
+    const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+#define SGC_DIRECT_PF(NS_)                                                                                      \
+  do {                                                                                                          \
+    allow_smem(k_spmm_direct_pf<T, NS_>, smem);                                                                 \
+    k_spmm_direct_pf<T, NS_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                         \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
+        colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
+  } while (0)
+    if (variant == 1 && per_lane <= 4) SGC_DIRECT_PF(4);
+    else if (variant == 1 && per_lane <= 8) SGC_DIRECT_PF(8);
+    else if (variant == 1 && per_lane <= 12) SGC_DIRECT_PF(12);
+    else launch_spmm_k<T, false, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
+#undef SGC_DIRECT_PF
   }
   ++*nk;
   if (g->n_heavy > 0) {
@@ -635,7 +729,7 @@ void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint3
   const int64_t tiles = (rows + R - 1) / R;
   k_ema<T, R, RPL><<<grid_for(tiles, 1, 1 << 30), kBlock, smem, st>>>(
       Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out, (int)op.cols_out,
-      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, rows, lb, sa, sp, so);
+      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, op.ema_sym ? 1 : 0, rows, lb, sa, sp, so);
 }
 
 template <typename T>

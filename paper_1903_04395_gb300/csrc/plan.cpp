@@ -313,15 +313,17 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
           tabs->push_back((uint32_t)c | (cr.rank_mask(rel_c) << 8));
         }
       }
-  } else if (kind == OP_EMA) {
+  } else if (kind == OP_EMA || kind == OP_EMA + 200) {
     // [j][S]: the j-th split of the (t-1)-subset S of the K relative colors into an
     // (a-1)-subset A (active child, minus the root's own color) and S \ A (passive
     // child), stored as two word offsets into the eMA block's shared memory, which
     // holds the active rows as [I(A)][row] and then the P rows as [I(S \ A)][row],
-    // row stride ema_rows + 1
+    // row stride ema_rows + 1.  The symmetric form (a table times itself, |A| = |S \ A|)
+    // keeps only the splits with I(A) < I(S \ A); the kernel doubles the sum.
+    const bool sym = kind == OP_EMA + 200;
     const int tt = t - 1, aa = a - 1;
     const uint64_t ct = cr.nsets(tt);
-    const uint64_t ns = cr.binom[tt][aa];
+    const uint64_t ns = sym ? cr.binom[tt][aa] / 2 : cr.binom[tt][aa];
     const uint32_t rs = (uint32_t)ema_rows + 1;
     std::vector<uint32_t> tab(2 * ns * ct);
     for (uint64_t s = 0; s < ct; ++s) {
@@ -329,9 +331,12 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
       uint64_t j = 0;
       for (uint32_t sub = m;; sub = (sub - 1) & m) {
         if (__builtin_popcount(sub) == aa) {
-          tab[2 * (j * ct + s)] = cr.rank_mask(sub) * rs;
-          tab[2 * (j * ct + s) + 1] = ((uint32_t)ema_ca + cr.rank_mask(m & ~sub)) * rs;
-          ++j;
+          const uint32_t ia = cr.rank_mask(sub), ip = cr.rank_mask(m & ~sub);
+          if (!sym || ia < ip) {
+            tab[2 * (j * ct + s)] = ia * rs;
+            tab[2 * (j * ct + s) + 1] = ((uint32_t)ema_ca + ip) * rs;
+            ++j;
+          }
         }
         if (sub == 0) break;
       }
@@ -539,7 +544,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       op.cols_out = w_table(C.size);
       op.ld_out = pad_ld(op.cols_out, elem);
       ema_shape(op.cols_a, op.cols_p, elem, g->smem_optin > 0 ? g->smem_optin : 227 * 1024, &op.ema_rows, &op.ema_rpl);
-      op.tab_off = build_tabs ? build_table(cr, k, OP_EMA, C.size, A.size, &P->tabs, &tcache, op.ema_rows, op.cols_a)
+      op.ema_sym = op.in_a == op.in_p && A.size - 1 == Pc.size;
+      if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
+      op.tab_off = build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
+                                            &P->tabs, &tcache, op.ema_rows, op.cols_a)
                               : 0;
       op.state_out = table_state[c] = n_states++;
       op.out = table_buf[c] = add_buf(P, "T" + std::to_string(c), rows * op.ld_out * elem, idx);

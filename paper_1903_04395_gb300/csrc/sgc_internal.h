@@ -137,6 +137,8 @@ struct PlanOp {
   bool spmm_buckets = false; // SpMM: sum neighbour rows per neighbour color, resolve once per row
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_rpl = 1;           // eMA: rows per lane
+  bool ema_sym = false;      // eMA of a table with itself (same buffer, |A| - 1 == |T_p|): each
+                             // unordered split once, doubled
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
   int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
   double alg_bytes = 0;      // algorithmic HBM bytes of one pass (tables read / written once)
