@@ -181,6 +181,57 @@ sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* 
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
                             int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
 
+/* --------------------------------------------------------------- serving -- */
+
+/*
+ * A counting server over one device-resident graph with continuous batching
+ * (the paper has no counterpart; it serves many color-coding queries on one
+ * graph).  Requests (template, colorings) queue on the host; a scheduler thread
+ * admits them in arrival order - looking past a request that does not fit yet -
+ * whenever their device workspace fits in the free part of `mem_budget` bytes
+ * (allocated once, at creation) and one of `max_inflight` execution slots is
+ * free.  Each admitted request runs its DP passes on its own stream, so requests
+ * overlap on the GPU.  Results are those of sgc_count for the same seeds and
+ * precision (FP32 within the FP32 tolerance: a request's batch size may differ).
+ * The graph and every submitted template must outlive the server.
+ */
+typedef struct sgc_server sgc_server;
+
+sgc_status sgc_server_create(const sgc_graph* g, int64_t mem_budget, int32_t max_inflight, sgc_server** out);
+
+/* Queue n colorings (host seeds, copied) of template t; *ticket identifies the request. */
+sgc_status sgc_server_submit(sgc_server* s, const sgc_template* t, const uint64_t* seeds, int32_t n,
+                             int32_t precision, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for a request.  On SGC_OK the request is
+ * retired and estimate, maps[n] (colorful maps per coloring) and latency_ms
+ * (submission to completion) are written where non-NULL.  SGC_ERR_TIMEOUT leaves
+ * the request pending (wait again); a request that failed returns its error
+ * (SGC_ERR_OOM when its workspace exceeds the whole budget) and is retired.
+ */
+sgc_status sgc_server_wait(sgc_server* s, uint64_t ticket, int32_t timeout_ms, double* estimate, double* maps,
+                           double* latency_ms);
+
+typedef struct sgc_server_stats {
+  int64_t completed;       /* requests finished successfully */
+  int64_t failed;          /* requests that failed or were cancelled */
+  int64_t pending;         /* queued, not admitted yet */
+  int32_t inflight;        /* admitted, running */
+  int32_t peak_inflight;   /* most requests running at once */
+  int64_t peak_bytes;      /* most budget bytes in use at once */
+  int64_t kernel_launches; /* kernels enqueued by the server */
+  double latency_p50_ms;   /* over completed requests, submission to completion */
+  double latency_p99_ms;
+  double queue_p50_ms;     /* submission to admission */
+  double span_s;           /* first submission to last completion */
+} sgc_server_stats;
+
+sgc_status sgc_server_stats_get(sgc_server* s, sgc_server_stats* out);
+
+/* Cancel queued requests, wait for running ones, release everything. */
+void sgc_server_destroy(sgc_server* s);
+
 /*
  * Counting without any device allocation (the paper has no counterpart:
  * this serves callers that cannot call cudaMalloc while they count, such as

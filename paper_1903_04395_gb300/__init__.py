@@ -52,6 +52,13 @@ class sgc_plan_info(ctypes.Structure):
                 ("est_bytes", ctypes.c_double), ("est_spmm_bytes", ctypes.c_double), ("est_fma", ctypes.c_double)]
 
 
+class sgc_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32), ("peak_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("queue_p50_ms", ctypes.c_double), ("span_s", ctypes.c_double)]
+
+
 class sgc_op_profile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("a", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("passes", ctypes.c_int64), ("kernels", ctypes.c_int64),
@@ -81,6 +88,13 @@ SIGNATURES = {
                                  _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sgc_count_device": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
     "sgc_count_device_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+    "sgc_server_create": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, _P(_vp)]),
+    "sgc_server_submit": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int32,
+                                         _P(ctypes.c_uint64)]),
+    "sgc_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int32, _P(ctypes.c_double),
+                                       _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "sgc_server_stats_get": (ctypes.c_int, [_vp, _P(sgc_server_stats)]),
+    "sgc_server_destroy": (None, [_vp]),
     "sgc_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "sgc_profile_read": (ctypes.c_int, [_vp, _P(sgc_op_profile), ctypes.c_int32, _P(ctypes.c_int32)]),
 }
@@ -226,6 +240,71 @@ def sgc_profile_read(g: int) -> list:
         e["name"] = OP_KINDS.get(e["kind"], str(e["kind"]))
         out.append(e)
     return out
+
+
+def sgc_server_create(g: int, mem_budget: int, max_inflight: int = 8) -> int:
+    out = _vp()
+    _check(lib().sgc_server_create(g, mem_budget, max_inflight, ctypes.byref(out)))
+    return out.value
+
+
+def sgc_server_submit(srv: int, t: int, seeds, precision: int = SGC_FP32) -> int:
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    ticket = ctypes.c_uint64(0)
+    _check(lib().sgc_server_submit(srv, t, s.ctypes.data_as(_P(ctypes.c_uint64)), int(s.size), precision,
+                                   ctypes.byref(ticket)))
+    return int(ticket.value)
+
+
+def sgc_server_wait(srv: int, ticket: int, n: int, timeout_ms: int = -1):
+    """Returns (estimate, maps[n], latency_ms); raises SgcError (SGC_ERR_TIMEOUT if not done in time)."""
+    est = ctypes.c_double(0)
+    lat = ctypes.c_double(0)
+    maps = np.zeros(max(n, 1), dtype=np.float64)
+    _check(lib().sgc_server_wait(srv, ticket, timeout_ms, ctypes.byref(est), maps.ctypes.data_as(_P(ctypes.c_double)),
+                                 ctypes.byref(lat)))
+    return float(est.value), maps[:n], float(lat.value)
+
+
+def sgc_server_stats_get(srv: int) -> dict:
+    st = sgc_server_stats()
+    _check(lib().sgc_server_stats_get(srv, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in sgc_server_stats._fields_}
+
+
+def sgc_server_destroy(srv: int) -> None:
+    lib().sgc_server_destroy(srv)
+
+
+class Server:
+    """Owning wrapper of an sgc_server handle (continuous-batching counting server)."""
+
+    def __init__(self, graph: "Graph", mem_budget: int, max_inflight: int = 8):
+        self.graph = graph  # keeps the graph alive
+        self.templates = {}
+        self.handle = sgc_server_create(graph.handle, mem_budget, max_inflight)
+
+    def submit(self, template: "Template", seeds, precision: str = "fp32") -> int:
+        self.templates[id(template)] = template  # keeps submitted templates alive
+        return sgc_server_submit(self.handle, template.handle, seeds,
+                                 SGC_FP64 if precision == "fp64" else SGC_FP32)
+
+    def wait(self, ticket: int, n: int, timeout_ms: int = -1):
+        return sgc_server_wait(self.handle, ticket, n, timeout_ms)
+
+    def stats(self) -> dict:
+        return sgc_server_stats_get(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------- wrappers --

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsgc.so")
-SOURCES = ["api.cpp", "plan.cpp", "graph.cu", "kernels.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "plan.cpp", "graph.cu", "kernels.cu", "noalloc.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -27,8 +27,6 @@ sgc_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SGC_ERR_OOM : SGC_ERR_CUDA;
 }
 
-namespace {
-
 int pow2_floor(int x) {
   int p = 1;
   while (p * 2 <= x) p *= 2;
@@ -63,6 +61,8 @@ sgc_status template_tables(const sgc_template* t, const Plan& plan, int device, 
   *out = d;
   return SGC_OK;
 }
+
+namespace {
 
 // One workspace per device, shared by every graph on it.  Passes on
 // different streams are ordered through `last`, an event recorded after the
@@ -102,6 +102,8 @@ sgc_status check_handles(const sgc_graph* g, const sgc_template* t) {
   return SGC_OK;
 }
 
+}  // namespace
+
 sgc_options resolve(const sgc_options* opt) {
   sgc_options o;
   sgc_options_init(&o);
@@ -129,6 +131,13 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) + " bytes of device workspace, limit " +
                                  std::to_string(mem_limit));
   const int root = p1.root, policy = p1.policy;
+  // Occupancy cap: a SpMM warp keeps a whole output row of `batch` colorings in
+  // shared memory, so wide rows take fewer colorings per pass (at most ~8 KB
+  // per warp keeps several blocks resident per SM).
+  int64_t widest = 0;
+  for (const PlanOp& op : p1.ops)
+    if (op.kind == OP_SPMM) widest = std::max<int64_t>(widest, op.ld_out * p1.elem);
+  while (bmax > 1 && widest * bmax > kSpmmRowBytesPerWarp) bmax /= 2;
   set->by_batch[1] = std::move(p1);
   set->bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
@@ -150,6 +159,8 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   *out = set;
   return SGC_OK;
 }
+
+namespace {
 
 sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t* seeds, int32_t n_iter,
                       const sgc_options* opt_in, bool device_io, double* estimate, double* maps_out) {

@@ -172,6 +172,16 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
 
 uint64_t automorphisms(const sgc_template* t);
 
+int pow2_floor(int x);
+sgc_options resolve(const sgc_options* opt);
+struct PlanSet;
+// Plans for every power-of-two batch up to bmax (capped for SpMM occupancy) whose
+// workspace fits mem_limit, cached on the graph; the caller holds g->mu.
+sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_options& o, int bmax, int64_t mem_limit,
+                        std::shared_ptr<PlanSet>* out);
+// Device copy of a plan's index tables, cached on the template by content.
+sgc_status template_tables(const sgc_template* t, const Plan& plan, int device, const uint32_t** out);
+
 sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, bool on_device,
                              uint32_t flags, cudaStream_t user_stream, sgc_graph** out);
 void graph_destroy_impl(sgc_graph* g);
@@ -193,6 +203,7 @@ inline int64_t spmm_bucket_bytes(int batch, int k, int64_t w_in, int elem) {
   return (int64_t)batch * k * w_in * elem;
 }
 constexpr int64_t kSpmmBucketMaxBytes = 4 * 1024;  // keeps ~48 warps per SM resident
+constexpr int64_t kSpmmRowBytesPerWarp = 8 * 1024;  // batch cap for wide SpMM output rows
 
 // Plans for the powers of two up to `bfit` colorings per pass (same root and
 // cut order), cached per graph.

@@ -1,0 +1,87 @@
+"""GPU parity at the benchmark's full sizes.
+
+* R-MAT scale 20 (edge factor 16, a=.57 b=.19 c=.19, seed 1), 10-vertex spider, k = 10,
+  8 colorings in one pass - the launch configuration bench.py times - against the exact
+  oracle on every coloring (the oracle's largest intermediate is ~2^100, so FP64 tables
+  are compared at relative 1e-12 and FP32 tables at 1e-5).
+* R-MAT scale 21 with the 12-vertex path, 13- and 15-vertex Pruefer trees (seeds 7, 9):
+  the exact oracle does not fit in memory there, so these are checked through properties
+  that hold at any size - FP32 against FP64 tables, and every DP root giving the same
+  count - while the same templates run against the oracle at reduced scale.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_04395_gb300 as sgc
+import sgcgen
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+FP32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    sgc.build()
+    rp, ci = sgcgen.rmat(20, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    return rp, ci, sgc.Graph(rp, ci)
+
+
+@pytest.fixture(scope="module")
+def rmat21():
+    sgc.build()
+    rp, ci = sgcgen.rmat(21, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    return rp, ci, sgc.Graph(rp, ci)
+
+
+def test_bench_workload_against_oracle(rmat20):
+    rp, ci, g = rmat20
+    parent = sgcgen.spider_tree([3, 3, 3])
+    seeds = list(range(1, 9))
+    t = sgc.Template(parent)
+    r32 = sgc.count(g, t, seeds, precision="fp32", batch=8)
+    r64 = sgc.count(g, t, seeds, precision="fp64", batch=8)
+    n = len(rp) - 1
+    for i, s in enumerate(seeds):
+        w = oracle.count(rp, ci, parent, oracle.colors(s, n, 10)).maps
+        assert abs(r64.maps[i] - w) <= 1e-12 * w, (s, r64.maps[i], w)
+        assert abs(r32.maps[i] - w) <= FP32_RTOL * w, (s, r32.maps[i], w, abs(r32.maps[i] - w) / w)
+
+
+@pytest.mark.parametrize("name,parent", [("path12", sgcgen.path_tree(12)), ("pruefer13", sgcgen.pruefer_tree(13, 7))])
+def test_scale21_fp32_against_fp64(rmat21, name, parent):
+    rp, ci, g = rmat21
+    t = sgc.Template(parent)
+    seeds = [1]
+    r32 = sgc.count(g, t, seeds, precision="fp32")
+    r64 = sgc.count(g, t, seeds, precision="fp64")
+    assert np.all(r64.maps > 0)
+    assert np.allclose(r32.maps, r64.maps, rtol=FP32_RTOL, atol=0), (name, r32.maps, r64.maps)
+
+
+def test_scale21_pruefer15_root_invariance(rmat21):
+    rp, ci, g = rmat21
+    parent = sgcgen.pruefer_tree(15, 9)
+    t = sgc.Template(parent)
+    base = sgc.count(g, t, [3], precision="fp32").maps[0]
+    assert base > 0 and np.isfinite(base)
+    for root in (0, 3, 14):
+        other = sgc.count(g, t, [3], precision="fp32", root=root).maps[0]
+        assert abs(other - base) <= 2 * FP32_RTOL * base, (root, other, base)
+
+
+def test_pruefer15_reduced_scale_against_oracle():
+    rp, ci = sgcgen.rmat(12, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    parent = sgcgen.pruefer_tree(15, 9)
+    g = sgc.Graph(rp, ci)
+    t = sgc.Template(parent)
+    seeds = [1, 2]
+    r32 = sgc.count(g, t, seeds, precision="fp32")
+    r64 = sgc.count(g, t, seeds, precision="fp64")
+    for i, s in enumerate(seeds):
+        res = oracle.count(rp, ci, parent, oracle.colors(s, len(rp) - 1, 15))
+        w = res.maps
+        tol64 = 0 if res.max_intermediate < 2 ** 53 else 1e-12
+        assert abs(r64.maps[i] - w) <= tol64 * w
+        assert abs(r32.maps[i] - w) <= FP32_RTOL * w
