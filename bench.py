@@ -39,6 +39,11 @@ WORKLOADS = {
     "serving": dict(scale=21, templates=[("pruefer3..14", ("pruefer", 8, 1))], batch=1, fp64=False,
                     desc="R-MAT scale 21 resident; Poisson stream (200 queries/s) of Pruefer trees with 3..14 "
                          "vertices and 1..32 colorings per query; admission under a 120 GB budget"),
+    "batched": dict(scale=20, templates=[(f"pruefer{k}", ("pruefer", k, 1000 + k)) for k in (5, 7, 8, 10, 11, 12)],
+                    batch=256, fp64=False, steps=1, warmup=3,
+                    desc="Erdos-Renyi G(n=500,000, m=6,000,000; seed 1) and R-MAT scale 20; Pruefer trees of "
+                         "5, 7, 8, 10, 11, 12 vertices (seeds 1000+size), 256 colorings each, all templates of a "
+                         "graph in one sgc_count_many call = one CUDA-graph launch; autotuned launch shapes"),
     "rmat21-trees": dict(scale=21, templates=[("path12", ("path", 12)), ("pruefer13", ("pruefer", 13, 7)),
                                               ("pruefer15", ("pruefer", 15, 9))], batch=4, fp64=False,
                          desc="R-MAT scale 21 (edge factor 16, a=.57 b=.19 c=.19, seed 1); 12-vertex path, "
@@ -49,8 +54,8 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 30; batched workload 1)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; batched workload 3)")
     ap.add_argument("--impl", choices=["sgc", "reference"], default="sgc")
     ap.add_argument("--workload", default="rmat20-spider10", choices=sorted(WORKLOADS))
     ap.add_argument("--no-fp64", action="store_true")
@@ -58,7 +63,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=32, help="serving workload: queries in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: offered queries per second")
-    return ap.parse_args()
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: planner launch shapes")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.steps is None:
+        args.steps = wl.get("steps", 30)
+    if args.warmup is None:
+        args.warmup = wl.get("warmup", 5)
+    return args
 
 
 def make_graph(wl):
@@ -204,6 +216,27 @@ def run_reference(args, wl, rank, world):
     scale-17 sample, scaled to the full workload by the ratio of the oracle's Lemma-1 work."""
     if rank != 0:
         return
+    if args_workload_name(wl) == "batched":
+        graphs = batched_graphs()
+        sizes = [(len(rp) - 1, len(ci)) for _, rp, ci in graphs]
+        for s in range(args.warmup):
+            batched_oracle_rate(wl, sizes, seed=1 + s)
+        rates, samples = [], []
+        for s in range(args.steps):
+            r = batched_oracle_rate(wl, sizes, seed=1 + args.warmup + s)
+            rates.append(r["value"])
+            samples.append(r)
+        value = len(rates) / sum(1.0 / r for r in rates)
+        cb = dict(samples[-1])
+        cb["value"] = value
+        colorings = 2 * len(wl["templates"]) * wl["batch"]
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "colorings/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * colorings / value,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128",
+               "data": "synthetic", "config": {"workload": "batched"}, "cpu_baseline": cb,
+               "e2e": {"value": value, "unit": "colorings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
     import oracle
     oracle.build()
     sample_scale = 17
@@ -317,6 +350,198 @@ def run_serving(args, wl, rank, world, local):
         print(json.dumps(res), flush=True)
 
 
+def batched_graphs():
+    """The batched workload's graphs: (name, row_ptr, col_idx)."""
+    import sgcgen
+    er = sgcgen.er(500_000, 6_000_000, seed=1)
+    rm = sgcgen.rmat(20, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    return [("er500k-d24", *er), ("rmat20", *rm)]
+
+
+def run_batched(args, wl, rank, world, local):
+    """Six templates x 256 colorings on two resident graphs; per graph one sgc_count_many call, recorded and
+    replayed as one CUDA graph (one launch for every pass of every template)."""
+    import torch
+    import paper_1903_04395_gb300 as sgc
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        sgc.build()
+    if dist:
+        dist.barrier()
+    sgc.lib()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    NC = wl["batch"]
+    parents = [make_parent(spec) for _, spec in wl["templates"]]
+    NT = len(parents)
+    graphs = []
+    for name, rp, ci in batched_graphs():
+        d_rp = torch.from_numpy(rp).cuda()
+        d_ci = torch.from_numpy(ci).cuda()
+        g = sgc.Graph.from_device(len(rp) - 1, len(ci), d_rp.data_ptr(), d_ci.data_ptr(), stream=stream.cuda_stream)
+        graphs.append((name, g, len(rp) - 1, len(ci), rp, ci))
+        del d_rp, d_ci
+    templates = [sgc.Template(p) for p in parents]
+    handles = [t.handle for t in templates]
+    opt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=0, stream=stream.cuda_stream, use_graph=1,
+                               autotune=0 if args.no_autotune else 1)
+    K, W = args.steps, args.warmup
+
+    def seeds_for(step, gi):
+        base = 1 + rank * 100_000_000 + (step * len(graphs) + gi) * NT * NC
+        return np.arange(base, base + NT * NC, dtype=np.uint64).reshape(NT, NC)
+
+    t_tune = time.perf_counter()
+    for gi, (_, g, *_r) in enumerate(graphs):
+        if not args.no_autotune:
+            for h in handles:
+                sgc.sgc_autotune(g.handle, h, sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=NC,
+                                                                   stream=stream.cuda_stream))
+    t_tune = time.perf_counter() - t_tune
+    for s in range(W):
+        for gi, (_, g, *_r) in enumerate(graphs):
+            sgc.sgc_count_many(g.handle, handles, seeds_for(s, gi), opt)
+    torch.cuda.synchronize()
+    launches0 = sum(g.stats()["kernel_launches"] for _, g, *_r in graphs)
+    per_graph = [0.0] * len(graphs)
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_all0 = torch.cuda.Event(enable_timing=True)
+    e_all1 = torch.cuda.Event(enable_timing=True)
+    e_all0.record(stream)
+    for s in range(W, W + K):
+        for gi, (_, g, *_r) in enumerate(graphs):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sgc.sgc_count_many(g.handle, handles, seeds_for(s, gi), opt)
+            b.record(stream)
+            b.synchronize()
+            per_graph[gi] += a.elapsed_time(b)
+    e_all1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.__exit__()
+    ms = e_all0.elapsed_time(e_all1)
+    if dist:
+        x = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms = float(x.item())
+    launches = sum(g.stats()["kernel_launches"] for _, g, *_r in graphs) - launches0
+    colorings = len(graphs) * NT * NC
+    res = {"metric": METRIC, "value": world * K * colorings / (ms / 1e3), "unit": "colorings/s", "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched", "graphs": ["Erdos-Renyi n=500,000 m=6,000,000 seed 1",
+                                                        "R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, seed 1"],
+                      "templates": [n for n, _ in wl["templates"]], "colorings_per_template": NC,
+                      "launch": "one sgc_count_many per graph = one CUDA-graph launch (recorded in warm-up)",
+                      "autotune": not args.no_autotune, "tables": "fp32 (power-of-two scaled), fp64 final reduction",
+                      "parallelism": f"colorings sharded over {world} GPU(s), no collective in the data path",
+                      "l2": "inputs larger than L2 (count tables of many GB per step)"},
+           "per_graph": [{"graph": graphs[i][0], "ms_per_step": per_graph[i] / K,
+                          "colorings_per_s": K * NT * NC / (per_graph[i] / 1e3)} for i in range(len(graphs))],
+           "autotune_s": t_tune, "gpu_launches": launches, "clocks": sampler.summary()}
+    if not args.no_autotune:
+        res["tuned_shapes"] = {}
+        for _, g, *_r in graphs[1:]:
+            for (name, _), h in zip(wl["templates"], handles):
+                rep = sgc.sgc_autotune(g.handle, h, sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=NC,
+                                                                         stream=stream.cuda_stream))
+                res["tuned_shapes"][name] = [
+                    (f"{e['name']}(t={e['t']},a={e['a']},p={e['p']})" if e["kind"] >= 0 else "batch") + ": " +
+                    ", ".join(f"{sh}={m:.2f}ms" for sh, m in zip(e["shapes"], e["ms"])) +
+                    f" -> {e['shapes'][e['chosen']]}" for e in rep]
+
+    # roofline: one profiled step per graph after the timed region (op by op, CUDA events per op)
+    peak, peak_kind = measured_peak()
+    ops = {}
+    popt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=0, stream=stream.cuda_stream, use_graph=0,
+                                autotune=opt.autotune)
+    for gi, (gname, g, *_r) in enumerate(graphs):
+        sgc.sgc_profile_enable(g.handle, True)
+        sgc.sgc_count_many(g.handle, handles, seeds_for(W + K, gi), popt)
+        for e in sgc.sgc_profile_read(g.handle):
+            key = f"{gname}:{e['name']}(t={e['t']},a={e['a']},p={e['p']},B={e['batch']})"
+            ops[key] = {"op": key, "kind": e["name"], "ms": e["ms"], "passes": e["passes"],
+                        "bytes": e["bytes"] * e["passes"]}
+        sgc.sgc_profile_enable(g.handle, False)
+    tot = sum(o["ms"] for o in ops.values()) or 1e-9
+    lst = sorted(ops.values(), key=lambda o: -o["ms"])
+    for o in lst:
+        o["share"] = o["ms"] / tot
+        o["gbs"] = o["bytes"] / (o["ms"] * 1e-3) / 1e9 if o["ms"] > 0 else 0.0
+    dom = lst[0]
+    res["roofline"] = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                       "frac": dom["gbs"] / peak, "traffic": None, "kernel": dom["op"],
+                       "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'})",
+                       "note": "from one op-by-op profiled step per graph after the timed region"}
+    res["ops"] = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in o.items()} for o in lst[:12]]
+
+    if not args.no_e2e:
+        # end to end through the public API with host buffers: graph upload from pinned host memory, every
+        # template's colorings from host seeds, results read back, graph released (planner shapes: tuning a
+        # freshly created graph would be timed too)
+        eopt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=0, use_graph=1)
+        pinned = [(torch.from_numpy(rp).pin_memory(), torch.from_numpy(ci).pin_memory(), n, nnz)
+                  for _, _, n, nnz, rp, ci in graphs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for gi, (h_rp, h_ci, n, nnz) in enumerate(pinned):
+            gh = sgc.sgc_graph_create(n, nnz, h_rp.data_ptr(), h_ci.data_ptr(), sgc.SGC_GRAPH_VALIDATE)
+            try:
+                sgc.sgc_count_many(gh, handles, seeds_for(W + K + 1, gi), eopt)
+            finally:
+                sgc.sgc_graph_destroy(gh)
+        dt = time.perf_counter() - t0
+        res["e2e"] = {"value": world * colorings / dt, "unit": "colorings/s", "steps": 1,
+                      "h2d_bytes_per_step": sum(4 * (n + 1) + 4 * nnz + 8 * NT * NC for _, _, n, nnz in pinned),
+                      "d2h_bytes_per_step": 8 * NT * NC * len(pinned),
+                      "includes": "graph upload + validation + renumbering, planning, recording, counting, "
+                                  "read-back, release"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = batched_oracle_rate(wl, [(n, nnz) for _, _, n, nnz, _, _ in graphs])
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def batched_oracle_rate(wl, full_sizes, sample_scale=15, seed=1):
+    """The oracle on one coloring of every template on an R-MAT sample, scaled to the whole batched job by
+    the oracle's Lemma-1 work ratio per (graph, template)."""
+    import oracle
+    import sgcgen
+    oracle.build()
+    rp, ci = sgcgen.rmat(sample_scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    sn, snnz = len(rp) - 1, len(ci)
+    NC = wl["batch"]
+    job_s, sample_s, colorings = 0.0, 0.0, 0
+    for _, spec in wl["templates"]:
+        parent = make_parent(spec)
+        k = len(parent)
+        t0 = time.perf_counter()
+        oracle.count(rp, ci, parent, oracle.colors(seed, sn, k))
+        dt = time.perf_counter() - t0
+        sample_s += dt
+        for n, nnz in full_sizes:
+            job_s += NC * dt * oracle_work(n, nnz, parent, k) / oracle_work(sn, snnz, parent, k)
+            colorings += NC
+    return {"value": colorings / job_s, "unit": "colorings/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"one coloring of each of the {len(wl['templates'])} templates on R-MAT scale {sample_scale} "
+                      f"({sn} vertices, {snnz} entries), {sample_s:.1f} s in all, scaled per graph and template by "
+                      f"the oracle's Lemma-1 work ratio to {colorings} colorings"}
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -329,6 +554,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, wl, rank, world, local)
+        return
+    if args.workload == "batched":
+        run_batched(args, wl, rank, world, local)
         return
 
     import torch

@@ -68,7 +68,20 @@ typedef struct sgc_options {
   int64_t mem_limit;   /* device workspace bytes this call may use; 0 = 90% of free memory */
   void* stream;        /* cudaStream_t to run on; NULL = the graph's own stream */
   int32_t root;        /* template vertex used as the DP root; -1 = cost-model choice */
-  int32_t use_graph;   /* 1 = replay the per-batch launch sequence as a CUDA graph (default) */
+  int32_t use_graph;   /* 1 (default) = record the call's whole launch sequence - every pass of
+                          every template - as one CUDA graph, cache it on the graph handle and
+                          replay it with one launch; 0 = launch op by op.  Profiling (below)
+                          always launches op by op. */
+  int32_t autotune;    /* 1 = before the first count of a template on a graph, time every
+                          candidate launch shape of each SpMM and eMA op (and the two largest
+                          batch sizes) on that graph and keep the fastest; cached with the
+                          plan.  0 (default) = the planner's shapes. */
+  int32_t spmm_shape;  /* force the SpMM launch shape: 1 direct, 2 direct with next-neighbour
+                          prefetch, 3 bucketed; ops it does not fit keep theirs.  0 (default) =
+                          planner or autotuner.  Results do not depend on it beyond FP32
+                          summation order. */
+  int32_t ema_rows;    /* force the rows an eMA block stages: 64, 32, 16, 8 or 4 (ops whose rows do
+                          not fit in shared memory keep theirs); 0 (default) = planner or autotuner */
 } sgc_options;
 
 /* Fill *opt with the defaults described above. */
@@ -180,6 +193,49 @@ sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* 
  */
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds,
                             int32_t n_iter, const sgc_options* opt, double* d_colorful_maps);
+
+/*
+ * Count several templates on one graph in one call.  Every coloring of every
+ * template is an independent iteration of the estimator of Section 2.1 (the
+ * iteration count of Section 5.1 is per template).  For template j,
+ * seeds[j * n_iter + i] (host) is the seed of its coloring i, and the results
+ * are colorful_maps[j * n_iter + i] and estimates[j] (host, either may be
+ * NULL), each equal to what sgc_count returns for that template and those
+ * seeds.  The passes of different templates run side by side on up to four
+ * streams (templates assigned longest first to the least loaded stream, fewer
+ * streams when their workspaces do not fit opt->mem_limit); with
+ * opt->use_graph the whole call - every pass of every template - is one CUDA
+ * graph launch, recorded on the first call and replayed on later calls with
+ * the same templates, n_iter and options (new seeds each time).
+ * Blocks until the results are on the host.
+ */
+sgc_status sgc_count_many(const sgc_graph* g, int32_t n_templates, const sgc_template* const* templates,
+                          const uint64_t* seeds, int32_t n_iter, const sgc_options* opt, double* estimates,
+                          double* colorful_maps);
+
+/* One op of a tuned plan: the launch shapes timed and the one kept. */
+typedef struct sgc_tune_entry {
+  int32_t kind;              /* as sgc_op_profile.kind */
+  int32_t t, a, p;           /* sub-template sizes */
+  int32_t batch;             /* colorings per pass of the plan tuned */
+  int32_t n_candidates;
+  int32_t chosen;            /* index of the kept shape in shapes[] */
+  int32_t shapes[8];         /* SpMM: 1 direct, 2 direct with prefetch, 3 bucketed;
+                                eMA: rows staged per block */
+  double ms[8];              /* device time of the op, one pass, per shape */
+} sgc_tune_entry;
+
+/*
+ * Launch shapes of the SpMM (Eq. 2, Section 4.5) and eMA (Section 4.5) steps
+ * only change how the same sums are scheduled; FP64 results are identical and
+ * FP32 results differ by summation order only.
+ * Run the autotuner for template t on graph g under *opt (as sgc_count with
+ * opt->autotune = 1 would before its first pass) and copy up to `cap` entries of
+ * its report to out; *n = entries available.  The batch sizes compared are
+ * reported with kind = -1, shapes[] = batch sizes and ms[] = time per coloring.
+ */
+sgc_status sgc_autotune(const sgc_graph* g, const sgc_template* t, const sgc_options* opt, sgc_tune_entry* out,
+                        int32_t cap, int32_t* n);
 
 /* --------------------------------------------------------------- serving -- */
 

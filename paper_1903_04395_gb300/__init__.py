@@ -37,7 +37,8 @@ class SgcError(RuntimeError):
 
 class sgc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("batch", ctypes.c_int32), ("mem_limit", ctypes.c_int64),
-                ("stream", ctypes.c_void_p), ("root", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("root", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("spmm_shape", ctypes.c_int32), ("ema_rows", ctypes.c_int32)]
 
 
 class sgc_graph_stats(ctypes.Structure):
@@ -65,6 +66,12 @@ class sgc_op_profile(ctypes.Structure):
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class sgc_tune_entry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("a", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("shapes", ctypes.c_int32 * 8), ("ms", ctypes.c_double * 8)]
+
+
 OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 4: "ema", 5: "final_leaf", 6: "final"}
 
 # exported symbols with their ctypes signatures (restype, argtypes)
@@ -87,6 +94,10 @@ SIGNATURES = {
     "sgc_count": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, _P(sgc_options),
                                  _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sgc_count_device": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+    "sgc_count_many": (ctypes.c_int, [_vp, ctypes.c_int32, _P(_vp), _P(ctypes.c_uint64), ctypes.c_int32,
+                                      _P(sgc_options), _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "sgc_autotune": (ctypes.c_int, [_vp, _vp, _P(sgc_options), _P(sgc_tune_entry), ctypes.c_int32,
+                                    _P(ctypes.c_int32)]),
     "sgc_count_device_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
     "sgc_server_create": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, _P(_vp)]),
     "sgc_server_submit": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int32,
@@ -131,10 +142,12 @@ def _i32(a):
 
 # ----------------------------------------------------------- C-named calls --
 
-def sgc_options_init(precision=SGC_FP32, batch=0, mem_limit=0, stream=None, root=-1, use_graph=1) -> sgc_options:
+def sgc_options_init(precision=SGC_FP32, batch=0, mem_limit=0, stream=None, root=-1, use_graph=1,
+                     autotune=0, spmm_shape=0, ema_rows=0) -> sgc_options:
     o = sgc_options()
     lib().sgc_options_init(ctypes.byref(o))
     o.precision, o.batch, o.mem_limit, o.root, o.use_graph = precision, batch, mem_limit, root, use_graph
+    o.autotune, o.spmm_shape, o.ema_rows = autotune, spmm_shape, ema_rows
     o.stream = stream
     return o
 
@@ -211,6 +224,39 @@ def sgc_count(g: int, t: int, seeds, opt: sgc_options | None = None, maps_out: n
 def sgc_count_device(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:
     """Device-buffer count: enqueue on opt.stream (or the graph's stream); no synchronisation."""
     _check(lib().sgc_count_device(g, t, d_seeds, n_iter, ctypes.byref(opt) if opt is not None else None, d_maps))
+
+
+def sgc_count_many(g: int, templates, seeds, opt: sgc_options | None = None):
+    """Several templates in one call: seeds has shape (n_templates, n_iter); returns
+    (estimates[n_templates], colorful maps[n_templates, n_iter])."""
+    handles = (_vp * max(len(templates), 1))(*templates)
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(len(templates), -1))
+    n_t, n_iter = s.shape
+    est = np.zeros(max(n_t, 1), dtype=np.float64)
+    maps = np.zeros(max(n_t * n_iter, 1), dtype=np.float64)
+    _check(lib().sgc_count_many(g, n_t, handles, s.ctypes.data_as(_P(ctypes.c_uint64)) if s.size else None, n_iter,
+                                ctypes.byref(opt) if opt is not None else None,
+                                est.ctypes.data_as(_P(ctypes.c_double)), maps.ctypes.data_as(_P(ctypes.c_double))))
+    return est[:n_t], maps[:n_t * n_iter].reshape(n_t, n_iter)
+
+
+SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets"}
+
+
+def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:
+    """Run (or read back) the autotuner for one template: per op, the launch shapes timed (ms, one pass)
+    and the one kept; the last entry (kind -1) compares batch sizes (ms per coloring)."""
+    cap = 64
+    buf = (sgc_tune_entry * cap)()
+    n = ctypes.c_int32(0)
+    _check(lib().sgc_autotune(g, t, ctypes.byref(opt) if opt is not None else None, buf, cap, ctypes.byref(n)))
+    out = []
+    for i in range(min(n.value, cap)):
+        e = buf[i]
+        m = e.n_candidates
+        out.append({"kind": e.kind, "name": OP_KINDS.get(e.kind, "batch"), "t": e.t, "a": e.a, "p": e.p,
+                    "batch": e.batch, "shapes": list(e.shapes[:m]), "ms": list(e.ms[:m]), "chosen": e.chosen})
+    return out
 
 
 SGC_STATIC_WORKSPACE_BYTES = 64 << 20
@@ -370,11 +416,22 @@ class CountResult:
 
 
 def count(graph: Graph, template: Template, seeds, precision: str = "fp32", batch: int = 0, root: int = -1,
-          mem_limit: int = 0) -> CountResult:
+          mem_limit: int = 0, use_graph: bool = True, autotune: bool = False, spmm_shape: int = 0,
+          ema_rows: int = 0) -> CountResult:
     opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root,
-                           mem_limit=mem_limit)
+                           mem_limit=mem_limit, use_graph=1 if use_graph else 0, autotune=1 if autotune else 0,
+                           spmm_shape=spmm_shape, ema_rows=ema_rows)
     est, maps = sgc_count(graph.handle, template.handle, seeds, opt)
     return CountResult(est, maps)
+
+
+def count_many(graph: Graph, templates, seeds, precision: str = "fp32", batch: int = 0, use_graph: bool = True,
+               autotune: bool = False, mem_limit: int = 0):
+    """Count several templates in one call (one CUDA-graph launch when use_graph): seeds (n_templates, n_iter).
+    Returns (estimates, maps[n_templates, n_iter])."""
+    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch,
+                           use_graph=1 if use_graph else 0, autotune=1 if autotune else 0, mem_limit=mem_limit)
+    return sgc_count_many(graph.handle, [t.handle for t in templates], seeds, opt)
 
 
 def plan(graph: Graph, template: Template, precision: str = "fp32", batch: int = 0, root: int = -1) -> dict:

@@ -117,16 +117,29 @@ sgc_options resolve(const sgc_options* opt) {
 sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_options& o, int bmax, int64_t mem_limit,
                         std::shared_ptr<PlanSet>* out) {
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
-                          "/" + std::to_string(bmax);
+                          "/" + std::to_string(bmax) + (o.autotune ? "/tuned" : "") + "/s" +
+                          std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows);
   for (auto& kv : g->plan_cache)
     if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
       *out = kv.second;
       return SGC_OK;
     }
   auto set = std::make_shared<PlanSet>();
+  const bool forced = o.spmm_shape != 0 || o.ema_rows != 0;
+  // forced launch shapes, as one code per op index of a plan
+  auto forced_shapes = [&](const Plan& p) {
+    std::vector<int> sh(p.ops.size(), 0);
+    for (size_t i = 0; i < p.ops.size(); ++i)
+      sh[i] = p.ops[i].kind == OP_SPMM ? o.spmm_shape : p.ops[i].kind == OP_EMA ? o.ema_rows : 0;
+    return sh;
+  };
   Plan p1;
   sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1);
   if (rc != SGC_OK) return rc;
+  if (forced) {
+    const std::vector<int> sh = forced_shapes(p1);
+    if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh)) != SGC_OK) return rc;
+  }
   if (p1.ws_bytes > mem_limit)
     return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) + " bytes of device workspace, limit " +
                                  std::to_string(mem_limit));
@@ -144,6 +157,10 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     Plan pb;
     rc = make_plan(g, t, o.precision, root, policy, b, true, &pb);
     if (rc != SGC_OK) return rc;
+    if (forced) {
+      const std::vector<int> sh = forced_shapes(pb);
+      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh)) != SGC_OK) return rc;
+    }
     if (pb.ws_bytes > mem_limit) break;
     set->by_batch[b] = std::move(pb);
     set->bfit = b;
@@ -162,89 +179,437 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
 
 namespace {
 
-sgc_status count_impl(const sgc_graph* g, const sgc_template* t, const uint64_t* seeds, int32_t n_iter,
-                      const sgc_options* opt_in, bool device_io, double* estimate, double* maps_out) {
-  sgc_status rc = check_handles(g, t);
+// ------------------------------------------------------------ autotuner
+// Times every candidate launch shape of each SpMM and eMA op of the plans for
+// the two largest batch sizes, on this graph, and keeps the fastest shape per
+// op and the batch size with the lower time per coloring.  Shapes only change
+// how the same sums are scheduled (Eq. 2 and the eMA of Section 4.5).
+
+struct TimedPass {
+  std::vector<double> op_ms;  // per op index
+  double total_ms = 0;
+};
+
+sgc_status time_pass(const sgc_graph* g, const Plan& plan, DevicePool& pool, cudaStream_t st, TimedPass* out) {
+  sgc_status rc = ensure_workspace(pool, plan.ws_bytes);
   if (rc != SGC_OK) return rc;
+  char* ws = static_cast<char*>(pool.ptr);
+  uint32_t* d_tabs = nullptr;
+  const size_t tab_bytes = std::max<size_t>(plan.tabs.size(), 4) * sizeof(uint32_t);
+  SGC_CUDA_TRY(cudaMalloc(&d_tabs, tab_bytes));
+  std::vector<uint64_t> seeds((size_t)plan.batch);
+  for (int b = 0; b < plan.batch; ++b) seeds[(size_t)b] = 0x5EEDull + (uint64_t)b;
+  cudaError_t e = cudaSuccess;
+  if (!plan.tabs.empty())
+    e = cudaMemcpyAsync(d_tabs, plan.tabs.data(), plan.tabs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + plan.bufs[plan.buf_seeds].offset, seeds.data(), seeds.size() * sizeof(uint64_t),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d_tabs);
+    return cuda_fail(e, "autotuner set-up");
+  }
+  Profiler prof;
+  prof.on = true;
+  prof.by_index = true;
+  int64_t nk = 0;
+  // one untimed pass (first-touch of the tables), then the timed one
+  rc = run_pass(g, plan, d_tabs, ws, st, nullptr, &nk);
+  if (rc == SGC_OK) rc = run_pass(g, plan, d_tabs, ws, st, &prof, &nk);
+  e = cudaStreamSynchronize(st);
+  out->op_ms.assign(plan.ops.size(), 0.0);
+  out->total_ms = 0;
+  for (auto& pe : prof.pending) {
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pe.e0, pe.e1);
+    out->op_ms[(size_t)pe.slot] += ms;
+    out->total_ms += ms;
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
+  cudaFree(d_tabs);
+  if (rc != SGC_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotuner pass");
+  return SGC_OK;
+}
+
+sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_options& o, PlanSet* set,
+                      DevicePool& pool, cudaStream_t st) {
+  std::vector<int> batches{set->bfit};
+  if (set->bfit >= 2 && set->by_batch.count(set->bfit / 2)) batches.push_back(set->bfit / 2);
+  std::vector<sgc_tune_entry> report;
+  sgc_tune_entry bt{};
+  bt.kind = -1;
+  int best_b = set->bfit;
+  double best_per = 0;
+  for (int b : batches) {
+    const Plan& base = set->by_batch.at(b);
+    const size_t nops = base.ops.size();
+    std::vector<std::vector<int>> cands(nops);
+    size_t ncand = 1;
+    for (size_t i = 0; i < nops; ++i) {
+      cands[i] = op_shape_candidates(g, base, (int)i);
+      if (cands[i].size() > 8) cands[i].resize(8);
+      ncand = std::max(ncand, cands[i].size());
+    }
+    std::vector<std::vector<double>> ms(nops, std::vector<double>(ncand, -1.0));
+    std::vector<double> fixed_ms(nops, 0.0);
+    for (size_t c = 0; c < ncand; ++c) {
+      std::vector<int> shapes(nops, 0);
+      for (size_t i = 0; i < nops; ++i)
+        if (!cands[i].empty()) shapes[i] = cands[i][std::min(c, cands[i].size() - 1)];
+      Plan p;
+      sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes);
+      if (rc != SGC_OK) return rc;
+      TimedPass tp;
+      if ((rc = time_pass(g, p, pool, st, &tp)) != SGC_OK) return rc;
+      for (size_t i = 0; i < nops; ++i) {
+        if (cands[i].empty()) {
+          fixed_ms[i] = c == 0 ? tp.op_ms[i] : std::min(fixed_ms[i], tp.op_ms[i]);
+        } else if (c < cands[i].size()) {
+          ms[i][c] = tp.op_ms[i];
+        }
+      }
+    }
+    std::vector<int> best(nops, 0);
+    double pass_ms = 0;
+    for (size_t i = 0; i < nops; ++i) {
+      if (cands[i].empty()) {
+        pass_ms += fixed_ms[i];
+        continue;
+      }
+      size_t arg = 0;
+      for (size_t c = 1; c < cands[i].size(); ++c)
+        if (ms[i][c] < ms[i][arg]) arg = c;
+      best[i] = cands[i][arg];
+      pass_ms += ms[i][arg];
+      const PlanOp& op = base.ops[i];
+      sgc_tune_entry te{};
+      te.kind = op.kind;
+      te.t = op.t;
+      te.a = op.a;
+      te.p = op.p;
+      te.batch = b;
+      te.n_candidates = (int32_t)cands[i].size();
+      te.chosen = (int32_t)arg;
+      for (size_t c = 0; c < cands[i].size(); ++c) {
+        te.shapes[c] = cands[i][c];
+        te.ms[c] = ms[i][c];
+      }
+      report.push_back(te);
+    }
+    Plan tuned;
+    sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best);
+    if (rc != SGC_OK) return rc;
+    set->by_batch[b] = std::move(tuned);
+    const double per = pass_ms / b;
+    bt.shapes[bt.n_candidates] = b;
+    bt.ms[bt.n_candidates] = per;
+    if (bt.n_candidates == 0 || per < best_per) {
+      best_per = per;
+      best_b = b;
+      bt.chosen = bt.n_candidates;
+    }
+    bt.n_candidates++;
+  }
+  bt.batch = best_b;
+  report.push_back(bt);
+  set->bfit = best_b;
+  set->tuned = true;
+  set->report = std::move(report);
+  return SGC_OK;
+}
+
+// --------------------------------------------------------------- counting
+
+struct Job {
+  const sgc_template* t = nullptr;
+  std::shared_ptr<PlanSet> plans;
+  std::map<int, const uint32_t*> d_tabs;  // device index tables per batch size
+  int lane = 0;                           // stream: 0 = the call's stream, l > 0 = g->lanes[l - 1]
+  double cost = 0;                        // cost-model seconds for all its colorings
+  int64_t ws = 0;                         // workspace of its largest pass
+};
+
+constexpr int kMaxLanes = 4;
+constexpr int64_t kAlign = 256;
+
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+sgc_status ensure_lanes(const sgc_graph* g, int n_lanes) {
+  while ((int)g->lanes.size() < n_lanes - 1) {
+    cudaStream_t s = nullptr;
+    SGC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    g->lanes.push_back(s);
+  }
+  while ((int)g->lane_events.size() < n_lanes) {
+    cudaEvent_t e = nullptr;
+    SGC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g->lane_events.push_back(e);
+  }
+  return SGC_OK;
+}
+
+// Every pass of every job.  Seeds are read from, and colorful maps written to,
+// the staging arrays at the front of the workspace (job j, coloring i at
+// j * n_iter + i), so that a recorded launch sequence serves any seeds.
+sgc_status enqueue_jobs(const sgc_graph* g, const std::vector<Job>& jobs, int n_lanes,
+                        const std::vector<int64_t>& lane_off, char* ws, const uint64_t* d_seeds, double* d_maps,
+                        int32_t n_iter, cudaStream_t st, Profiler* prof, int64_t* kernels) {
+  if (n_lanes > 1) {
+    SGC_CUDA_TRY(cudaEventRecord(g->lane_events[0], st));
+    for (int l = 1; l < n_lanes; ++l) SGC_CUDA_TRY(cudaStreamWaitEvent(g->lanes[l - 1], g->lane_events[0], 0));
+  }
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    const Job& J = jobs[j];
+    cudaStream_t ls = J.lane == 0 ? st : g->lanes[J.lane - 1];
+    char* w = ws + lane_off[J.lane];
+    for (int32_t i = 0; i < n_iter;) {
+      int b = J.plans->bfit;
+      while (b > n_iter - i) b /= 2;
+      const Plan& plan = J.plans->by_batch.at(b);
+      const size_t at = j * (size_t)n_iter + (size_t)i;
+      SGC_CUDA_TRY(cudaMemcpyAsync(w + plan.bufs[plan.buf_seeds].offset, d_seeds + at, sizeof(uint64_t) * b,
+                                   cudaMemcpyDeviceToDevice, ls));
+      sgc_status rc = run_pass(g, plan, J.d_tabs.at(b), w, ls, prof, kernels);
+      if (rc != SGC_OK) return rc;
+      SGC_CUDA_TRY(cudaMemcpyAsync(d_maps + at, w + plan.bufs[plan.buf_out].offset, sizeof(double) * b,
+                                   cudaMemcpyDeviceToDevice, ls));
+      i += b;
+    }
+  }
+  if (n_lanes > 1) {
+    for (int l = 1; l < n_lanes; ++l) {
+      SGC_CUDA_TRY(cudaEventRecord(g->lane_events[l], g->lanes[l - 1]));
+      SGC_CUDA_TRY(cudaStreamWaitEvent(st, g->lane_events[l], 0));
+    }
+  }
+  return SGC_OK;
+}
+
+// Record the jobs' launch sequence as one CUDA graph (or reuse the recording
+// made by an earlier call with the same key) and launch it on st.
+sgc_status launch_recorded(const sgc_graph* g, const std::string& key, const std::vector<Job>& jobs, int n_lanes,
+                           const std::vector<int64_t>& lane_off, char* ws, const uint64_t* d_seeds, double* d_maps,
+                           int32_t n_iter, cudaStream_t st) {
+  for (auto& x : g->exec_cache)
+    if (x.key == key && x.ws == ws) {
+      SGC_CUDA_TRY(cudaGraphLaunch(x.exec, st));
+      g->kernel_launches += x.kernels;
+      return SGC_OK;
+    }
+  int64_t nk = 0;
+  SGC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  sgc_status rc = enqueue_jobs(g, jobs, n_lanes, lane_off, ws, d_seeds, d_maps, n_iter, st, nullptr, &nk);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc != SGC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "recording the launch sequence");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "instantiating the launch sequence");
+  ExecEntry x;
+  x.key = key;
+  x.exec = exec;
+  x.ws = ws;
+  x.kernels = nk;
+  for (const Job& J : jobs) x.plans.push_back(J.plans);
+  if (g->exec_cache.size() >= 16) {
+    cudaGraphExecDestroy(g->exec_cache.front().exec);
+    g->exec_cache.erase(g->exec_cache.begin());
+  }
+  g->exec_cache.push_back(std::move(x));
+  SGC_CUDA_TRY(cudaGraphLaunch(exec, st));
+  g->kernel_launches += nk;
+  return SGC_OK;
+}
+
+// The counting driver behind sgc_count, sgc_count_device and sgc_count_many:
+// n_t templates, n_iter colorings each; seeds[j * n_iter + i] is coloring i of
+// template j (host or, with device_io, device), maps the same layout.
+sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const* ts, const uint64_t* seeds,
+                      int32_t n_iter, const sgc_options* opt_in, bool device_io, double* estimates, double* maps_out) {
+  if (!g) return fail(SGC_ERR_INVALID, "graph is NULL");
+  if (n_t < 0) return fail(SGC_ERR_INVALID, "n_templates must be >= 0");
+  if (n_t > 0 && !ts) return fail(SGC_ERR_INVALID, "templates is NULL");
+  for (int32_t j = 0; j < n_t; ++j)
+    if (!ts[j]) return fail(SGC_ERR_INVALID, "template is NULL");
   if (n_iter < 0) return fail(SGC_ERR_INVALID, "n_iter must be >= 0");
-  if (n_iter > 0 && !seeds) return fail(SGC_ERR_INVALID, "seeds is NULL");
-  if (device_io && n_iter > 0 && !maps_out) return fail(SGC_ERR_INVALID, "colorful_maps is NULL");
+  if (n_iter > 0 && n_t > 0 && !seeds) return fail(SGC_ERR_INVALID, "seeds is NULL");
+  if (device_io && n_iter > 0 && n_t > 0 && !maps_out) return fail(SGC_ERR_INVALID, "colorful_maps is NULL");
   const sgc_options o = resolve(opt_in);
   if (o.precision != SGC_FP32 && o.precision != SGC_FP64) return fail(SGC_ERR_INVALID, "unknown precision");
-  if (o.root >= t->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
+  for (int32_t j = 0; j < n_t; ++j)
+    if (o.root >= ts[j]->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmBuckets)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..3");
+  if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
+      o.ema_rows != 4)
+    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8 or 4");
   SGC_CUDA_TRY(cudaSetDevice(g->device));
   std::lock_guard<std::mutex> lock(g->mu);
   DevicePool& pool = device_pool(g->device);
   std::lock_guard<std::mutex> pool_lock(pool.mu);
   cudaStream_t st = o.stream ? (cudaStream_t)o.stream : g->stream;
-  const int k = t->k;
-  if (estimate) *estimate = 0.0;
-  if (n_iter == 0) return SGC_OK;
+  if (estimates)
+    for (int32_t j = 0; j < n_t; ++j) estimates[j] = 0.0;
+  if (n_iter == 0 || n_t == 0) return SGC_OK;
+  sgc_status rc = SGC_OK;
+  const size_t total = (size_t)n_t * (size_t)n_iter;
+  std::vector<double> host_maps(total, 0.0);
 
-  std::vector<double> host_maps(device_io ? 0 : (size_t)n_iter);
-  if (k == 1 || g->n_act == 0) {
-    // one vertex: every vertex is a colorful map; no edges: nothing maps
-    const double v = k == 1 ? (double)g->n : 0.0;
-    if (device_io) {
-      std::vector<double> tmp((size_t)n_iter, v);
-      SGC_CUDA_TRY(cudaMemcpyAsync(maps_out, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-      SGC_CUDA_TRY(cudaStreamSynchronize(st));
+  // templates with one vertex, and graphs without edges, need no DP
+  std::vector<Job> jobs;
+  std::vector<int32_t> job_of(n_t, -1);
+  bool special_only = true;
+  for (int32_t j = 0; j < n_t; ++j) {
+    if (ts[j]->k == 1 || g->n_act == 0) {
+      const double v = ts[j]->k == 1 ? (double)g->n : 0.0;
+      std::fill(host_maps.begin() + (size_t)j * n_iter, host_maps.begin() + (size_t)(j + 1) * n_iter, v);
     } else {
-      std::fill(host_maps.begin(), host_maps.end(), v);
+      special_only = false;
     }
-  } else {
+  }
+
+  if (!special_only) {
     size_t free_b = 0, total_b = 0;
     SGC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const int64_t mem_limit = o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + pool.bytes) * 0.9);
+    const int64_t staging = 2 * align_up((int64_t)(total * sizeof(double)));
+    const int64_t mem_limit =
+        (o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + pool.bytes) * 0.9)) - staging;
+    if (mem_limit <= 0) return fail(SGC_ERR_OOM, "no device memory left for the workspace");
     const int bmax = pow2_floor(std::min(32, o.batch > 0 ? o.batch : std::max(1, (int)n_iter)));
-    std::shared_ptr<PlanSet> plans;
-    rc = plan_batches(g, t, o, bmax, mem_limit, &plans);
-    if (rc != SGC_OK) return rc;
-    const Plan& top = plans->by_batch.at(plans->bfit);
-    // every batch size has its own plan and index tables (the SpMM form can
-    // depend on the batch), each uploaded once and cached by content
-    std::map<int, const uint32_t*> d_tabs_by_batch;
-    for (auto& kv : plans->by_batch) {
-      const uint32_t* d = nullptr;
-      if ((rc = template_tables(t, kv.second, g->device, &d)) != SGC_OK) return rc;
-      d_tabs_by_batch[kv.first] = d;
+    for (int32_t j = 0; j < n_t; ++j) {
+      if (ts[j]->k == 1 || g->n_act == 0) continue;
+      Job J;
+      J.t = ts[j];
+      if ((rc = plan_batches(g, ts[j], o, bmax, mem_limit, &J.plans)) != SGC_OK) return rc;
+      if (o.autotune && !J.plans->tuned && o.spmm_shape == 0 && o.ema_rows == 0) {
+        if (pool.last) SGC_CUDA_TRY(cudaEventSynchronize(pool.last));
+        if ((rc = tune_plans(g, ts[j], o, J.plans.get(), pool, st)) != SGC_OK) return rc;
+      }
+      // every batch size has its own plan and index tables (the SpMM form can
+      // depend on the batch), each uploaded once and cached by content
+      for (auto& kv : J.plans->by_batch) {
+        const uint32_t* d = nullptr;
+        if ((rc = template_tables(ts[j], kv.second, g->device, &d)) != SGC_OK) return rc;
+        J.d_tabs[kv.first] = d;
+        J.ws = std::max(J.ws, kv.second.ws_bytes);
+      }
+      const Plan& top = J.plans->by_batch.at(J.plans->bfit);
+      J.cost = top.est_cost * (double)n_iter;
+      job_of[j] = (int32_t)jobs.size();
+      jobs.push_back(std::move(J));
     }
-    if ((rc = ensure_workspace(pool, top.ws_bytes)) != SGC_OK) return rc;
+
+    // side-by-side streams: longest job first onto the least loaded stream,
+    // fewer streams while the workspaces do not fit
+    std::vector<size_t> order(jobs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return jobs[x].cost > jobs[y].cost; });
+    int n_lanes = std::min<int>(kMaxLanes, (int)jobs.size());
+    std::vector<int64_t> lane_ws;
+    for (;; --n_lanes) {
+      std::vector<double> load((size_t)n_lanes, 0.0);
+      lane_ws.assign((size_t)n_lanes, 0);
+      for (size_t x : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        jobs[x].lane = l;
+        load[(size_t)l] += jobs[x].cost;
+        lane_ws[(size_t)l] = std::max(lane_ws[(size_t)l], align_up(jobs[x].ws));
+      }
+      int64_t sum = 0;
+      for (int64_t w : lane_ws) sum += w;
+      if (sum <= mem_limit || n_lanes == 1) break;
+    }
+    std::vector<int64_t> lane_off((size_t)n_lanes, 0);
+    int64_t ws_total = staging;
+    for (int l = 0; l < n_lanes; ++l) {
+      lane_off[(size_t)l] = ws_total;
+      ws_total += lane_ws[(size_t)l];
+    }
+    if ((rc = ensure_lanes(g, n_lanes)) != SGC_OK) return rc;
+    if ((rc = ensure_workspace(pool, ws_total)) != SGC_OK) return rc;
     if (!pool.last) SGC_CUDA_TRY(cudaEventCreateWithFlags(&pool.last, cudaEventDisableTiming));
     SGC_CUDA_TRY(cudaStreamWaitEvent(st, pool.last, 0));
     char* ws = static_cast<char*>(pool.ptr);
-    Profiler* prof = g->prof.on ? &g->prof : nullptr;
-    for (int32_t i = 0; i < n_iter;) {
-      int b = plans->bfit;
-      while (b > n_iter - i) b /= 2;
-      const Plan& plan = plans->by_batch.at(b);
-      char* d_seeds = ws + plan.bufs[plan.buf_seeds].offset;
-      char* d_out = ws + plan.bufs[plan.buf_out].offset;
-      SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds + i, sizeof(uint64_t) * b,
-                                   device_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      if ((rc = run_pass(g, plan, d_tabs_by_batch.at(b), ws, st, prof, &g->kernel_launches)) != SGC_OK) return rc;
+    uint64_t* d_seeds = reinterpret_cast<uint64_t*>(ws);
+    double* d_maps = reinterpret_cast<double*>(ws + staging / 2);
+
+    // seeds of the jobs, in job order
+    std::vector<uint64_t> job_seeds;
+    if (!device_io) job_seeds.resize(jobs.size() * (size_t)n_iter);
+    for (int32_t j = 0; j < n_t; ++j) {
+      if (job_of[j] < 0) continue;
+      const size_t dst = (size_t)job_of[j] * n_iter, src = (size_t)j * n_iter;
       if (device_io) {
-        SGC_CUDA_TRY(cudaMemcpyAsync(maps_out + i, d_out, sizeof(double) * b, cudaMemcpyDeviceToDevice, st));
+        SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds + dst, seeds + src, sizeof(uint64_t) * n_iter,
+                                     cudaMemcpyDeviceToDevice, st));
       } else {
-        SGC_CUDA_TRY(cudaMemcpyAsync(host_maps.data() + i, d_out, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+        std::copy(seeds + src, seeds + src + n_iter, job_seeds.begin() + dst);
       }
-      i += b;
+    }
+    if (!device_io)
+      SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds, job_seeds.data(), job_seeds.size() * sizeof(uint64_t),
+                                   cudaMemcpyHostToDevice, st));
+
+    Profiler* prof = g->prof.on ? &g->prof : nullptr;
+    if (o.use_graph && !prof) {
+      std::string key = "n" + std::to_string(n_iter) + "/l" + std::to_string(n_lanes);
+      for (const Job& J : jobs)
+        key += "/" + std::to_string(J.t->uid) + ":" + std::to_string(reinterpret_cast<uintptr_t>(J.plans.get())) +
+               ":" + std::to_string(J.plans->bfit) + ":" + std::to_string(J.lane);
+      rc = launch_recorded(g, key, jobs, n_lanes, lane_off, ws, d_seeds, d_maps, n_iter, st);
+    } else {
+      rc = enqueue_jobs(g, jobs, n_lanes, lane_off, ws, d_seeds, d_maps, n_iter, st, prof, &g->kernel_launches);
+    }
+    if (rc != SGC_OK) return rc;
+
+    // results back, template order
+    for (int32_t j = 0; j < n_t; ++j) {
+      if (job_of[j] < 0) continue;
+      const size_t src = (size_t)job_of[j] * n_iter, dst = (size_t)j * n_iter;
+      if (device_io) {
+        SGC_CUDA_TRY(cudaMemcpyAsync(maps_out + dst, d_maps + src, sizeof(double) * n_iter,
+                                     cudaMemcpyDeviceToDevice, st));
+      } else {
+        SGC_CUDA_TRY(cudaMemcpyAsync(host_maps.data() + dst, d_maps + src, sizeof(double) * n_iter,
+                                     cudaMemcpyDeviceToHost, st));
+      }
     }
     SGC_CUDA_TRY(cudaEventRecord(pool.last, st));
-    if (!device_io) SGC_CUDA_TRY(cudaStreamSynchronize(st));
-    SGC_CUDA_TRY(cudaGetLastError());
   }
-  if (!device_io) {
-    if (maps_out) std::memcpy(maps_out, host_maps.data(), sizeof(double) * (size_t)n_iter);
-    if (estimate) {
+  if (device_io) {
+    // templates that needed no DP
+    bool copied = false;
+    for (int32_t j = 0; j < n_t; ++j)
+      if (job_of[j] < 0) {
+        SGC_CUDA_TRY(cudaMemcpyAsync(maps_out + (size_t)j * n_iter, host_maps.data() + (size_t)j * n_iter,
+                                     sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
+        copied = true;
+      }
+    if (copied) SGC_CUDA_TRY(cudaStreamSynchronize(st));  // host_maps is released on return
+    SGC_CUDA_TRY(cudaGetLastError());
+    return SGC_OK;
+  }
+  SGC_CUDA_TRY(cudaStreamSynchronize(st));
+  SGC_CUDA_TRY(cudaGetLastError());
+  if (maps_out) std::memcpy(maps_out, host_maps.data(), sizeof(double) * total);
+  if (estimates)
+    for (int32_t j = 0; j < n_t; ++j) {
+      const int k = ts[j]->k;
       long double scale = 1.0L;
       for (int i = 1; i <= k; ++i) scale *= (long double)k / (long double)i;  // k^k / k!
       long double s = 0;
-      for (double m : host_maps) s += (long double)m;
-      *estimate = (double)(s / (long double)n_iter / (long double)t->aut * scale);
+      for (int32_t i = 0; i < n_iter; ++i) s += (long double)host_maps[(size_t)j * n_iter + (size_t)i];
+      estimates[j] = (double)(s / (long double)n_iter / (long double)ts[j]->aut * scale);
     }
-  }
   return SGC_OK;
 }
 
@@ -263,6 +628,9 @@ void sgc_options_init(sgc_options* opt) {
   opt->stream = nullptr;
   opt->root = -1;
   opt->use_graph = 1;
+  opt->autotune = 0;
+  opt->spmm_shape = 0;
+  opt->ema_rows = 0;
 }
 
 const char* sgc_last_error(void) { return g_last_error.c_str(); }
@@ -383,12 +751,52 @@ sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_opt
 
 sgc_status sgc_count(const sgc_graph* g, const sgc_template* t, const uint64_t* seeds, int32_t n_iter,
                      const sgc_options* opt, double* estimate, double* colorful_maps) {
-  return count_impl(g, t, seeds, n_iter, opt, false, estimate, colorful_maps);
+  if (!t) return fail(SGC_ERR_INVALID, "template is NULL");
+  return count_core(g, 1, &t, seeds, n_iter, opt, false, estimate, colorful_maps);
 }
 
 sgc_status sgc_count_device(const sgc_graph* g, const sgc_template* t, const uint64_t* d_seeds, int32_t n_iter,
                             const sgc_options* opt, double* d_colorful_maps) {
-  return count_impl(g, t, d_seeds, n_iter, opt, true, nullptr, d_colorful_maps);
+  if (!t) return fail(SGC_ERR_INVALID, "template is NULL");
+  return count_core(g, 1, &t, d_seeds, n_iter, opt, true, nullptr, d_colorful_maps);
+}
+
+sgc_status sgc_count_many(const sgc_graph* g, int32_t n_templates, const sgc_template* const* templates,
+                          const uint64_t* seeds, int32_t n_iter, const sgc_options* opt, double* estimates,
+                          double* colorful_maps) {
+  return count_core(g, n_templates, templates, seeds, n_iter, opt, false, estimates, colorful_maps);
+}
+
+sgc_status sgc_autotune(const sgc_graph* g, const sgc_template* t, const sgc_options* opt, sgc_tune_entry* out,
+                        int32_t cap, int32_t* n) {
+  sgc_status rc = check_handles(g, t);
+  if (rc != SGC_OK) return rc;
+  if (!n || (cap > 0 && !out)) return fail(SGC_ERR_INVALID, "NULL argument");
+  sgc_options o = resolve(opt);
+  o.autotune = 1;
+  if (o.precision != SGC_FP32 && o.precision != SGC_FP64) return fail(SGC_ERR_INVALID, "unknown precision");
+  if (o.root >= t->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
+  *n = 0;
+  if (t->k == 1) return SGC_OK;
+  SGC_CUDA_TRY(cudaSetDevice(g->device));
+  std::lock_guard<std::mutex> lock(g->mu);
+  if (g->n_act == 0) return SGC_OK;
+  DevicePool& pool = device_pool(g->device);
+  std::lock_guard<std::mutex> pool_lock(pool.mu);
+  cudaStream_t st = o.stream ? (cudaStream_t)o.stream : g->stream;
+  size_t free_b = 0, total_b = 0;
+  SGC_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const int64_t mem_limit = o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + pool.bytes) * 0.9);
+  const int bmax = pow2_floor(std::min(32, o.batch > 0 ? o.batch : 32));
+  std::shared_ptr<PlanSet> plans;
+  if ((rc = plan_batches(g, t, o, bmax, mem_limit, &plans)) != SGC_OK) return rc;
+  if (!plans->tuned) {
+    if (pool.last) SGC_CUDA_TRY(cudaEventSynchronize(pool.last));
+    if ((rc = tune_plans(g, t, o, plans.get(), pool, st)) != SGC_OK) return rc;
+  }
+  *n = (int32_t)plans->report.size();
+  for (int32_t i = 0; i < *n && i < cap; ++i) out[i] = plans->report[(size_t)i];
+  return SGC_OK;
 }
 
 sgc_status sgc_profile_enable(const sgc_graph* g, int32_t on) {

@@ -120,6 +120,10 @@ void destroy_graph(sgc_graph* g) {
     cudaEventDestroy(pe.e0);
     cudaEventDestroy(pe.e1);
   }
+  for (auto& x : g->exec_cache)
+    if (x.exec) cudaGraphExecDestroy(x.exec);
+  for (cudaStream_t s : g->lanes) cudaStreamDestroy(s);
+  for (cudaEvent_t e : g->lane_events) cudaEventDestroy(e);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
 }
@@ -299,6 +303,7 @@ void graph_destroy_impl(sgc_graph* g) {
   if (!g) return;
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->stream);
+  for (cudaStream_t s : g->lanes) cudaStreamSynchronize(s);
   destroy_graph(g);
 }
 

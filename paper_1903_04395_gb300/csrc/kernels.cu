@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_direct_pf(
     for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
     const int cvk = (int)((color_word(colors, it.row, batch, word) >> shift) & 0xffu) * k;
     __syncwarp();
-    int32_t u_n = __ldg(col_idx + it.lo);
+    int32_t u_n = it.lo < it.hi ? __ldg(col_idx + it.lo) : 0;
     uint64_t cw_n = color_word(colors, u_n, batch, word);
     for (int32_t e = it.lo; e < it.hi; ++e) {
       const int32_t u = u_n;
@@ -630,17 +630,6 @@ __global__ void k_final_sum(const double* __restrict__ partials, int nblocks, in
   out[b] = s;
 }
 
-// Direct SpMM variant: 0 = chunked loop (default), 1 = next-neighbour prefetch
-// with all loads of a neighbour in flight (measured equal on R-MAT 20, more
-// registers); SGC_SPMM_DIRECT overrides.
-int spmm_direct_variant() {
-  static const int v = [] {
-    const char* e = std::getenv("SGC_SPMM_DIRECT");
-    return e ? std::atoi(e) : 0;
-  }();
-  return v;
-}
-
 template <typename KernelT>
 void allow_smem(KernelT kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -695,7 +684,7 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
       launch_spmm_k<T, true, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
   } else {
     const int64_t per_lane = (op.cols_p + 32 / batch - 1) / (32 / batch);
-    const int variant = spmm_direct_variant();
+    const int variant = op.spmm_variant;
     const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
 #define SGC_DIRECT_PF(NS_)                                                                                      \
   do {                                                                                                          \
@@ -789,12 +778,18 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
 
   if (fp32) SGC_CUDA_TRY(cudaMemsetAsync(states, 0, sizeof(ScaleState) * (size_t)std::max(1, plan.n_states), st));
   int64_t nk = 0;
-  for (const PlanOp& op : plan.ops) {
+  for (size_t oi = 0; oi < plan.ops.size(); ++oi) {
+    const PlanOp& op = plan.ops[oi];
     int slot = -1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const int64_t nk0 = nk;
     if (prof) {
-      slot = profile_slot(prof, op, B);
+      if (prof->by_index) {
+        if (prof->agg.size() < plan.ops.size()) prof->agg.resize(plan.ops.size());
+        slot = (int)oi;
+      } else {
+        slot = profile_slot(prof, op, B);
+      }
       SGC_CUDA_TRY(cudaEventCreate(&e0));
       SGC_CUDA_TRY(cudaEventCreate(&e1));
       SGC_CUDA_TRY(cudaEventRecord(e0, st));

@@ -14,6 +14,7 @@
 // * Workspace layout: every buffer's lifetime in op order and a first-fit
 //   placement in one device arena.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <map>
 #include <string>
@@ -401,8 +402,28 @@ static void use_buf(Plan* P, int buf, int op) {
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
 }
 
+// Direct SpMM loop used when no tuned shape says otherwise: 0 = chunked (the
+// default), 1 = next-neighbour prefetch (measured equal on R-MAT 20 with more
+// registers); SGC_SPMM_DIRECT overrides.
+static int default_spmm_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("SGC_SPMM_DIRECT");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
+
+// Bucketed SpMM rows the autotuner may try (the planner's own limit is
+// kSpmmBucketMaxBytes): up to 24 KB per warp still keeps 9 warps per SM.
+constexpr int64_t kSpmmBucketTuneMaxBytes = 24 * 1024;
+
+static int64_t spmm_cols_per_lane(int batch, int64_t cols_p) {
+  const int lanes_per_col = 32 / batch;
+  return (cols_p + lanes_per_col - 1) / lanes_per_col;
+}
+
 static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy,
-                     int batch, bool build_tabs, Plan* P) {
+                     int batch, bool build_tabs, Plan* P, const std::vector<int>* shapes = nullptr) {
   Rooted R;
   root_tree(t, root, &R);
   Builder B(R, policy);
@@ -484,6 +505,19 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.ld_p = table_ld[C.p];
         op.state_p = table_state[C.p];
         op.spmm_buckets = spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketMaxBytes;
+        op.spmm_variant = op.spmm_buckets ? 0 : default_spmm_variant();
+        const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
+        if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
+          op.spmm_buckets = true;
+          op.spmm_variant = 0;
+        } else if (shape == kShapeSpmmDirect) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 0;
+        } else if (shape == kShapeSpmmPrefetch && spmm_cols_per_lane(batch, op.cols_p) <= 12) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 1;
+        }
+        op.shape = op.spmm_buckets ? kShapeSpmmBuckets : op.spmm_variant ? kShapeSpmmPrefetch : kShapeSpmmDirect;
         op.tab_off = build_tabs ? build_table(cr, k, op.spmm_buckets ? (OpKind)(OP_SPMM + 100) : OP_SPMM, Pc.size,
                                               0, &P->tabs, &tcache)
                                 : 0;
@@ -543,7 +577,15 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       op.kind = OP_EMA;
       op.cols_out = w_table(C.size);
       op.ld_out = pad_ld(op.cols_out, elem);
-      ema_shape(op.cols_a, op.cols_p, elem, g->smem_optin > 0 ? g->smem_optin : 227 * 1024, &op.ema_rows, &op.ema_rpl);
+      const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
+      ema_shape(op.cols_a, op.cols_p, elem, smem_cap, &op.ema_rows, &op.ema_rpl);
+      const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
+      if ((shape == 64 || shape == 32 || shape == 16 || shape == 8 || shape == 4) &&
+          (op.cols_a + op.cols_p) * elem * (shape + 1) <= smem_cap) {
+        op.ema_rows = shape;
+        op.ema_rpl = shape == 64 ? 2 : 1;
+      }
+      op.shape = op.ema_rows;
       op.ema_sym = op.in_a == op.in_p && A.size - 1 == Pc.size;
       if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
       op.tab_off = build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
@@ -612,8 +654,24 @@ static bool tables_in_range(const Plan& P, int k) {
   return true;
 }
 
+std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
+  std::vector<int> c;
+  const PlanOp& op = P.ops[i];
+  const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
+  if (op.kind == OP_SPMM) {
+    c.push_back(kShapeSpmmDirect);
+    if (spmm_cols_per_lane(P.batch, op.cols_p) <= 12) c.push_back(kShapeSpmmPrefetch);
+    if (spmm_bucket_bytes(P.batch, P.k, op.cols_p, P.elem) <= kSpmmBucketTuneMaxBytes) c.push_back(kShapeSpmmBuckets);
+  } else if (op.kind == OP_EMA) {
+    for (int r : {64, 32, 16, 8})
+      if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap) c.push_back(r);
+  }
+  if (c.size() < 2) c.clear();
+  return c;
+}
+
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out) {
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes) {
   if (root >= t->k) return fail(SGC_ERR_INVALID, "options.root is not a template vertex");
   int best_root = -1, best_policy = 0;
   double best_cost = 0;
@@ -633,7 +691,7 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
       }
     }
   }
-  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out);
+  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out, shapes);
   if (build_tabs && !tables_in_range(*out, t->k)) return fail(SGC_ERR_INTERNAL, "index table out of range");
   return SGC_OK;
 }

@@ -60,11 +60,21 @@ struct PendingEvent {
 
 struct Profiler {
   bool on = false;
+  bool by_index = false;   // one slot per op index of the plan (autotuner) instead of per op kind
   std::vector<OpProfile> agg;
   std::vector<PendingEvent> pending;
 };
 
 struct PlanSet;
+
+// A recorded launch sequence of one counting call, replayed with one launch.
+struct ExecEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  void* ws = nullptr;                 // workspace the graph was recorded on
+  int64_t kernels = 0;                // kernel nodes in the graph
+  std::vector<std::shared_ptr<PlanSet>> plans;  // keeps the plans (and their keys) alive
+};
 
 }  // namespace sgc
 
@@ -92,6 +102,9 @@ struct sgc_graph {
   mutable int64_t kernel_launches = 0;    // kernels enqueued by calls on this handle
   mutable std::vector<std::pair<std::string, std::shared_ptr<sgc::PlanSet>>> plan_cache;
   std::vector<int32_t> h_degree_sorted;  // degrees in new numbering (host copy)
+  mutable std::vector<cudaStream_t> lanes;       // side streams for templates counted side by side
+  mutable std::vector<cudaEvent_t> lane_events;  // fork (0) and join (1..) events of those streams
+  mutable std::vector<sgc::ExecEntry> exec_cache;
 };
 
 struct sgc_template {
@@ -135,6 +148,8 @@ struct PlanOp {
   int64_t cols_p = 0, ld_p = 0;
   int64_t nsplit = 0;        // binom(t, p)
   bool spmm_buckets = false; // SpMM: sum neighbour rows per neighbour color, resolve once per row
+  int spmm_variant = 0;      // direct SpMM loop: 0 chunked, 1 next-neighbour prefetch
+  int shape = 0;             // launch shape code (kSpmm* / eMA rows), see op_shape_candidates
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_rpl = 1;           // eMA: rows per lane
   bool ema_sym = false;      // eMA of a table with itself (same buffer, |A| - 1 == |T_p|): each
@@ -164,11 +179,21 @@ struct Plan {
   int64_t scratch_width = 0;
 };
 
+// Launch-shape codes an autotuner may pick per op (0 keeps the planner's choice).
+// SpMM: the direct form with its chunked loop, the direct form with a
+// next-neighbour prefetch, or the bucketed form; eMA: the rows a block stages.
+constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3;
+
 // Plan the DP for template t on graph g.  root < 0 and policy < 0 let the
 // cost model choose; batch is the number of colorings per pass.  Index tables
-// are only built when build_tabs is set.
+// are only built when build_tabs is set.  `shapes`, when given, holds one
+// launch-shape code per op index (0 = default); codes that do not fit the
+// op (shared memory, form) are ignored.
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out);
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr);
+
+// The launch shapes worth timing for op `i` of plan p (empty: nothing to choose).
+std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& p, int i);
 
 uint64_t automorphisms(const sgc_template* t);
 
@@ -210,6 +235,8 @@ constexpr int64_t kSpmmRowBytesPerWarp = 8 * 1024;  // batch cap for wide SpMM o
 struct PlanSet {
   std::map<int, Plan> by_batch;
   int bfit = 1;
+  bool tuned = false;                 // by_batch[bfit] (and the next smaller) carry timed shapes
+  std::vector<sgc_tune_entry> report; // what the autotuner measured
 };
 
 }  // namespace sgc

@@ -1,0 +1,138 @@
+"""Several templates in one call, the recorded launch sequence and the launch shapes.
+
+* sgc_count_many (templates counted side by side on several streams, one CUDA
+  graph launch) returns, per template, what sgc_count returns alone - and the
+  exact oracle's colorful maps (FP64 exactly, FP32 within 1e-5).
+* A recorded launch sequence replays with new seeds (the seeds are staged, not
+  baked into the recording).
+* Every forced SpMM and eMA launch shape gives the oracle's counts; the
+  autotuner's report is well formed and its tuned plan counts the same.
+The shapes only reschedule the sums of Eq. 2 and of the eMA (Section 4.5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_04395_gb300 as sgc
+import sgcgen
+
+pytestmark = pytest.mark.gpu
+
+FP32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def er_graph():
+    sgc.build()
+    rp, ci = sgcgen.er(3000, 15000, 21)
+    return rp, ci, sgc.Graph(rp, ci)
+
+
+def parents():
+    return [sgcgen.path_tree(3), sgcgen.pruefer_tree(5, 1005), sgcgen.pruefer_tree(7, 1007),
+            sgcgen.spider_tree([2, 2, 1]), sgcgen.star_tree(6), np.array([-1], dtype=np.int32)]
+
+
+class Exact(np.ndarray):
+    """Oracle maps, remembering whether every intermediate count stayed below 2^53."""
+
+
+def oracle_maps(rp, ci, parent, seeds):
+    n = len(rp) - 1
+    res = [oracle.count(rp, ci, parent, oracle.colors(int(s), n, len(parent))) for s in seeds]
+    out = np.array([r.maps for r in res], dtype=np.float64).view(Exact)
+    out.exact = all(r.max_intermediate < 2 ** 53 for r in res)
+    return out
+
+
+def check(got, want, precision):
+    if precision == "fp64":
+        if getattr(want, "exact", True):
+            assert np.array_equal(got, np.asarray(want)), (got, want)
+        else:  # FP64 rounding once counts pass 2^53
+            assert np.allclose(got, np.asarray(want), rtol=1e-12, atol=0), (got, want)
+    else:
+        assert np.allclose(got, np.asarray(want), rtol=FP32_RTOL, atol=0), (got, want)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_many_matches_single_and_oracle(er_graph, precision, use_graph):
+    rp, ci, g = er_graph
+    ps = parents()
+    ts = [sgc.Template(p) for p in ps]
+    n_iter = 11  # passes of 8 + 2 + 1 colorings
+    seeds = np.arange(len(ts) * n_iter, dtype=np.uint64).reshape(len(ts), n_iter) * 7 + 3
+    est, maps = sgc.count_many(g, ts, seeds, precision=precision, use_graph=use_graph)
+    assert maps.shape == (len(ts), n_iter)
+    for j, (p, t) in enumerate(zip(ps, ts)):
+        single = sgc.count(g, t, seeds[j], precision=precision, use_graph=False)
+        if precision == "fp64":
+            assert np.array_equal(maps[j], single.maps), (j, maps[j], single.maps)
+            assert est[j] == pytest.approx(single.estimate, rel=1e-15)
+        else:
+            assert np.allclose(maps[j], single.maps, rtol=1e-6, atol=0)
+        check(maps[j], oracle_maps(rp, ci, p, seeds[j]), precision)
+
+
+def test_recorded_sequence_replays_with_new_seeds(er_graph):
+    rp, ci, g = er_graph
+    ps = parents()[1:4]
+    ts = [sgc.Template(p) for p in ps]
+    n_iter = 5
+    launches = []
+    for call in range(3):
+        seeds = np.arange(len(ts) * n_iter, dtype=np.uint64).reshape(len(ts), n_iter) + 1000 * (call + 1)
+        k0 = g.stats()["kernel_launches"]
+        _, maps = sgc.count_many(g, ts, seeds, precision="fp64", use_graph=True)
+        launches.append(g.stats()["kernel_launches"] - k0)
+        for j, p in enumerate(ps):
+            check(maps[j], oracle_maps(rp, ci, p, seeds[j]), "fp64")
+    # the replays launch the same recorded kernels
+    assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
+
+
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_spmm_shape(precision, spmm_shape):
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=3)
+    g = sgc.Graph(rp, ci)
+    for parent in (sgcgen.pruefer_tree(8, 1008), sgcgen.spider_tree([3, 3, 3])):
+        t = sgc.Template(parent)
+        seeds = np.arange(1, 12, dtype=np.uint64)  # 8 + 2 + 1
+        r = sgc.count(g, t, seeds, precision=precision, spmm_shape=spmm_shape)
+        check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
+
+
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4])
+def test_every_ema_rows(ema_rows):
+    sgc.build()
+    rp, ci = sgcgen.rmat(12, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=4)
+    g = sgc.Graph(rp, ci)
+    for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8)):
+        t = sgc.Template(parent)
+        seeds = np.arange(20, 29, dtype=np.uint64)  # 8 + 1
+        r = sgc.count(g, t, seeds, precision="fp64", ema_rows=ema_rows)
+        check(r.maps, oracle_maps(rp, ci, parent, seeds), "fp64")
+
+
+def test_autotune_report_and_tuned_counts():
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=5)
+    g = sgc.Graph(rp, ci)
+    parent = sgcgen.pruefer_tree(8, 1008)
+    t = sgc.Template(parent)
+    opt = sgc.sgc_options_init(precision=sgc.SGC_FP64, batch=8)
+    rep = sgc.sgc_autotune(g.handle, t.handle, opt)
+    assert rep and rep[-1]["kind"] == -1
+    assert rep[-1]["shapes"][rep[-1]["chosen"]] in (8, 4)
+    for e in rep[:-1]:
+        assert e["kind"] in (2, 4)
+        assert len(e["shapes"]) >= 2 and 0 <= e["chosen"] < len(e["shapes"])
+        assert all(ms > 0 for ms in e["ms"])
+    # a second call reads the cached report
+    assert sgc.sgc_autotune(g.handle, t.handle, opt) == rep
+    seeds = np.arange(1, 12, dtype=np.uint64)
+    tuned = sgc.count(g, t, seeds, precision="fp64", batch=8, autotune=True)
+    check(tuned.maps, oracle_maps(rp, ci, parent, seeds), "fp64")
