@@ -51,6 +51,9 @@ WORKLOADS = {
 }
 
 
+WORKLOAD_SCALE = {name: wl["scale"] for name, wl in WORKLOADS.items()}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -63,9 +66,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=32, help="serving workload: queries in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: offered queries per second")
-    ap.add_argument("--no-autotune", action="store_true", help="batched workload: planner launch shapes")
+    ap.add_argument("--no-autotune", action="store_true", help="planner launch shapes instead of the autotuner's")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="R-MAT scale override (small cases for profiling; not a bench configuration)")
+    ap.add_argument("--batch", type=int, default=None, help="colorings per pass override")
+    ap.add_argument("--spmm-shape", type=int, default=0, help="force an SpMM launch shape (sgc_options.spmm_shape)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.scale is not None:
+        wl["scale"] = args.scale
+    if args.batch is not None:
+        wl["batch"] = args.batch
     if args.steps is None:
         args.steps = wl.get("steps", 30)
     if args.warmup is None:
@@ -273,7 +284,9 @@ def run_reference(args, wl, rank, world):
 
 
 def config_of(wl, world):
-    return {"workload": args_workload_name(wl), "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
+    return {"workload": args_workload_name(wl) + ("" if wl["scale"] == WORKLOAD_SCALE.get(args_workload_name(wl))
+                                                  else f" (scale {wl['scale']} override)"),
+            "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
             % wl["scale"], "templates": [name for name, _ in wl["templates"]], "k": "|T|",
             "colorings_per_step_per_gpu": wl["batch"] * len(wl["templates"]),
             "tables": "fp32 (power-of-two scaled), fp64 final reduction",
@@ -638,12 +651,24 @@ def main():
             sgc.sgc_profile_enable(g.handle, False)
         return ms, launches, prof, (sampler.summary() if sampler else None)
 
-    opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream)
+    tune = 0 if (args.no_autotune or args.spmm_shape) else 1
+    opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream,
+                                 spmm_shape=args.spmm_shape, autotune=tune)
     ms, launches, prof, clocks = timed(opt32, W, K, profile=True, clocks=True)
     value = world * K * B * NT / (ms / 1e3)
     res = {"metric": METRIC, "value": value, "unit": "colorings/s", "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": config_of(wl, world)}
+    res["config"]["autotune"] = bool(tune)
+    if tune:
+        res["tuned_shapes"] = {}
+        for name, t in templates:
+            rep = sgc.sgc_autotune(g.handle, t.handle, opt32)
+            res["tuned_shapes"][name] = [
+                (f"{e['name']}(t={e['t']},a={e['a']},p={e['p']},B={e['batch']})" if e["kind"] >= 0 else "batch") +
+                ": " + ", ".join(f"{sgc.SHAPE_NAMES.get(sh, sh) if e['kind'] == 2 else sh}={m:.2f}ms"
+                                 for sh, m in zip(e["shapes"], e["ms"])) +
+                f" -> {e['shapes'][e['chosen']]}" for e in rep]
     if NT > 1:
         per = {}
         for ti, a, b_ in tpl_events:

@@ -240,7 +240,9 @@ def sgc_count_many(g: int, templates, seeds, opt: sgc_options | None = None):
     return est[:n_t], maps[:n_t * n_iter].reshape(n_t, n_iter)
 
 
-SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets"}
+SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buckets", 5: "direct+packed", 6: "direct+ring2",
+               7: "direct+ring4", 8: "direct-batch",
+               9: "direct-batch+lane-table", 10: "buckets-batch"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:

@@ -236,8 +236,9 @@ sgc_status time_pass(const sgc_graph* g, const Plan& plan, DevicePool& pool, cud
 
 sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_options& o, PlanSet* set,
                       DevicePool& pool, cudaStream_t st) {
+  // the largest batch and up to two halvings: wide rows favour smaller batches
   std::vector<int> batches{set->bfit};
-  if (set->bfit >= 2 && set->by_batch.count(set->bfit / 2)) batches.push_back(set->bfit / 2);
+  for (int b = set->bfit / 2; b >= 1 && batches.size() < 3 && set->by_batch.count(b); b /= 2) batches.push_back(b);
   std::vector<sgc_tune_entry> report;
   sgc_tune_entry bt{};
   bt.kind = -1;
@@ -447,8 +448,8 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
   for (int32_t j = 0; j < n_t; ++j)
     if (o.root >= ts[j]->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmBuckets)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..3");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmBucketsB)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..10");
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4)
     return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8 or 4");

@@ -242,13 +242,27 @@ __device__ __forceinline__ uint64_t color_word(const uint8_t* __restrict__ color
 // fetched 32 at a time and shuffled, and the next neighbour's color word and
 // row entries are loaded while the current one is added.  NSMAX = 0: plain
 // loop for wide rows.
-template <typename T, bool BUCKETS, int NSMAX>
+//
+// The direct form's position table is either 32-bit entries read through L1
+// (PT = 0; row stride w_in) or packed 1- or 2-byte entries staged in shared
+// memory (PT = 1, 2; row stride tab_ld): the lanes of one coloring then read
+// one shared word, so a warp's lookup touches a few banks instead of eight
+// L1 lines.  All-ones entries are >= ld_out and so dropped.
+template <int PT>
+__device__ __forceinline__ uint32_t spmm_pos_at(const uint32_t* tab, int64_t i) {
+  if (PT == 1) return reinterpret_cast<const uint8_t*>(tab)[i];
+  if (PT == 2) return reinterpret_cast<const uint16_t*>(tab)[i];
+  return tab[i];
+}
+
+template <typename T, bool BUCKETS, int NSMAX, int PT>
 __global__ void __launch_bounds__(kBlock) k_spmm(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
     int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k, int p,
     const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int w_out, int ld_out, T* __restrict__ scratch,
-    const uint32_t* __restrict__ tab_g, int tab_words_smem, const ScaleState* st_in, ScaleState* st_out) {
+    const uint32_t* __restrict__ tab_g, int tab_words_smem, int tab_ld, const ScaleState* st_in,
+    ScaleState* st_out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -310,10 +324,10 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
                 if (q < ns) qrow[step * q] += x[q];
             }
           } else {
-            const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+            const int64_t pt = (int64_t)(cvk + cu) * tab_ld + jl;
             uint32_t pos[NU];
 #pragma unroll
-            for (int q = 0; q < NU; ++q) pos[q] = q < ns ? pt[L * q] : 0xFFFFFFFFu;
+            for (int q = 0; q < NU; ++q) pos[q] = q < ns ? spmm_pos_at<PT>(tab, pt + L * q) : 0xFFFFFFFFu;
 #pragma unroll
             for (int q = 0; q < NU; ++q)
               if (pos[q] < (uint32_t)ld_out) acc[pos[q] * batch + b] += x[q];
@@ -335,12 +349,12 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
             for (int q = 0; q < ns; ++q) qrow[step * q] += __ldg(src + (int64_t)step * q);
           }
         } else {
-          const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+          const int64_t pt = (int64_t)(cvk + cu) * tab_ld + jl;
           int q = 0;
           for (; q + 4 <= ns; q += 4) {
             // the gathers do not wait for the positions (memory-level parallelism)
-            const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)];
-            const uint32_t p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
+            const uint32_t p0 = spmm_pos_at<PT>(tab, pt + L * q), p1 = spmm_pos_at<PT>(tab, pt + L * (q + 1));
+            const uint32_t p2 = spmm_pos_at<PT>(tab, pt + L * (q + 2)), p3 = spmm_pos_at<PT>(tab, pt + L * (q + 3));
             const T x0 = __ldg(src + (int64_t)step * q), x1 = __ldg(src + (int64_t)step * (q + 1));
             const T x2 = __ldg(src + (int64_t)step * (q + 2)), x3 = __ldg(src + (int64_t)step * (q + 3));
             if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += x0;
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(
             if (p3 < (uint32_t)ld_out) acc[p3 * batch + b] += x3;
           }
           for (; q < ns; ++q) {
-            const uint32_t p0 = pt[L * q];
+            const uint32_t p0 = spmm_pos_at<PT>(tab, pt + L * q);
             if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += __ldg(src + (int64_t)step * q);
           }
         }
@@ -455,6 +469,449 @@ __global__ void __launch_bounds__(kBlock) k_spmm_direct_pf(
     if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
   }
 }
+
+// Direct form with the batch B as a compile-time constant.  Lane l serves
+// coloring l % B and the entries j = l / B + (32 / B) q, which sit at
+// row[l + 32 q] of the neighbour's interleaved row, so the gathers and the
+// accumulator addresses are immediate offsets from per-neighbour bases.  The
+// position table is either the 32-bit [c_v][c_u][j] one (LM = false) or
+// lane-major with 16-bit entries (tab16[c_v][c_u][jl][q], nsp entries per
+// lane, all ones = nowhere), from which a lane reads four positions with one
+// 8-byte load (LM = true; faster for some widths and batches, slower for
+// others: the autotuner picks).  Neighbour ids and their color words are read
+// 32 at a time, one per lane, and shuffled.  Same summation order as k_spmm's
+// direct form.
+template <typename T, int B, bool LM>
+__global__ void __launch_bounds__(kBlock) k_spmm_d(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, const T* __restrict__ Min, int w_in,
+    int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch, const uint32_t* __restrict__ tab, int nsp,
+    const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int L = 32 / B;
+  constexpr int NW = B > 8 ? B / 8 : 1;  // color words per vertex
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = ld_out * B;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const int b = lane % B, jl = lane / B;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int64_t row_len = (int64_t)ld_in * B;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  const uint16_t* tab16 = reinterpret_cast<const uint16_t*>(tab);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = (int)((color_word(colors, it.row, B, word) >> shift) & 0xffu) * k;
+    __syncwarp();
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int cnt = min(32, it.hi - e0);
+      const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+      uint64_t w_lane[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) w_lane[w] = color_word(colors, u_lane, B, w);
+      for (int t = 0; t < cnt; ++t) {
+        const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
+        uint64_t cw = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t x = __shfl_sync(0xffffffffu, w_lane[w], t);
+          if (w == word) cw = x;
+        }
+        const int cu = (int)((cw >> shift) & 0xffu);
+        const T* src = Min + (int64_t)u * row_len + lane;
+        if (LM) {  // lane-major 16-bit table: four positions per load
+          const uint16_t* pt = tab16 + ((int64_t)(cvk + cu) * L + jl) * nsp;
+          for (int q = 0; q < ns; q += 4) {
+            const uint2 pv = __ldg(reinterpret_cast<const uint2*>(pt + q));
+            const uint32_t p0 = pv.x & 0xffffu, p1 = pv.x >> 16, p2 = pv.y & 0xffffu, p3 = pv.y >> 16;
+            const T x0 = __ldg(src + 32 * q);
+            const T x1 = q + 1 < ns ? __ldg(src + 32 * (q + 1)) : T(0);
+            const T x2 = q + 2 < ns ? __ldg(src + 32 * (q + 2)) : T(0);
+            const T x3 = q + 3 < ns ? __ldg(src + 32 * (q + 3)) : T(0);
+            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
+            if (p1 < (uint32_t)ld_out) acc[p1 * B + b] += x1;
+            if (p2 < (uint32_t)ld_out) acc[p2 * B + b] += x2;
+            if (p3 < (uint32_t)ld_out) acc[p3 * B + b] += x3;
+          }
+        } else {  // 32-bit table [c_v][c_u][j]
+          const uint32_t* pt = tab + (cvk + cu) * w_in + jl;
+          int q = 0;
+          for (; q + 4 <= ns; q += 4) {
+            const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)], p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
+            const T x0 = __ldg(src + 32 * q), x1 = __ldg(src + 32 * (q + 1));
+            const T x2 = __ldg(src + 32 * (q + 2)), x3 = __ldg(src + 32 * (q + 3));
+            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
+            if (p1 < (uint32_t)ld_out) acc[p1 * B + b] += x1;
+            if (p2 < (uint32_t)ld_out) acc[p2 * B + b] += x2;
+            if (p3 < (uint32_t)ld_out) acc[p3 * B + b] += x3;
+          }
+          for (; q < ns; ++q) {
+            const uint32_t p0 = pt[L * q];
+            const T x0 = __ldg(src + 32 * q);
+            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    T* dst = it.heavy ? scratch + item * (int64_t)acc_len : P + (int64_t)it.row * acc_len;
+    for (int i = lane; i < acc_len; i += 32) {
+      const T x = acc[i];
+      dst[i] = x;
+      if (!it.heavy) m = fmaxf(m, (float)x);
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
+// Bucketed form with the batch B as a compile-time constant: a lane's entries
+// of a neighbour's row are row[l + 32 q] and land in bucket row
+// Q[c(u)][l + 32 q] (no lookup, conflict-free), neighbour ids and color words
+// are shuffled from one load per 32 neighbours, and in the resolve step a
+// lane only ever serves its own coloring (B divides 32), so v's color is the
+// one already in a register.  The resolve table is staged in shared memory
+// when small (tab_words_smem words).  Same sums, in the same order, as
+// k_spmm's bucketed form.
+template <typename T, int B>
+__global__ void __launch_bounds__(kBlock) k_spmm_bk(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, int p, const T* __restrict__ Min,
+    int w_in, int ld_in, T* __restrict__ P, int w_out, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ tab_g, int tab_words_smem, const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int L = 32 / B;
+  constexpr int NW = B > 8 ? B / 8 : 1;
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = k * w_in * B;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const uint32_t* tab = tab_g;
+  if (tab_words_smem > 0) {
+    uint32_t* stab = reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(sm_raw) + (int64_t)wpb * acc_len);
+    for (int i = threadIdx.x; i < tab_words_smem; i += blockDim.x) stab[i] = __ldg(tab_g + i);
+    __syncthreads();
+    tab = stab;
+  }
+  const int b = lane % B, jl = lane / B;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int64_t row_len = (int64_t)ld_in * B;
+  const int bucket_len = w_in * B;
+  const int out_len = ld_out * B;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cv = (int)((color_word(colors, it.row, B, word) >> shift) & 0xffu);
+    __syncwarp();
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int cnt = min(32, it.hi - e0);
+      const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+      uint64_t w_lane[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) w_lane[w] = color_word(colors, u_lane, B, w);
+      for (int t = 0; t < cnt; ++t) {
+        const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
+        uint64_t cw = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t x = __shfl_sync(0xffffffffu, w_lane[w], t);
+          if (w == word) cw = x;
+        }
+        const int cu = (int)((cw >> shift) & 0xffu);
+        if (cu != cv) {  // a neighbour of v's own color never contributes
+          T* qrow = acc + cu * bucket_len + lane;
+          const T* src = Min + (int64_t)u * row_len + lane;
+          int q = 0;
+          for (; q + 4 <= ns; q += 4) {
+            const T x0 = __ldg(src + 32 * q), x1 = __ldg(src + 32 * (q + 1));
+            const T x2 = __ldg(src + 32 * (q + 2)), x3 = __ldg(src + 32 * (q + 3));
+            qrow[32 * q] += x0;
+            qrow[32 * (q + 1)] += x1;
+            qrow[32 * (q + 2)] += x2;
+            qrow[32 * (q + 3)] += x3;
+          }
+          for (; q < ns; ++q) qrow[32 * q] += __ldg(src + 32 * q);
+        }
+        __syncwarp();
+      }
+    }
+    // resolve: P(v, S) = sum over the colors c of S of Q[c][index of S - c relative to c]
+    T* dst = it.heavy ? scratch + item * (int64_t)out_len : P + (int64_t)it.row * out_len;
+    const uint32_t* ent0 = tab + (int64_t)cv * w_out * p;
+    for (int i = lane; i < out_len; i += 32) {
+      const int S = i / B;
+      T val = T(0);
+      if (S < w_out) {
+        const uint32_t* ent = ent0 + (int64_t)S * p;
+        for (int t = 0; t < p; ++t) {
+          const uint32_t e = ent[t];
+          const int c = (int)(e & 0xffu), j = (int)(e >> 8);
+          if (c < k && j < w_in) val += acc[(c * w_in + j) * B + b];
+        }
+      }
+      dst[i] = val;
+      if (!it.heavy) m = fmaxf(m, (float)val);
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
+// Direct form with the neighbour rows streamed into shared memory by
+// asynchronous copies (cp.async, 16 bytes per lane), R neighbours ahead of the
+// one being added: a warp keeps R rows (and their color bytes) in flight
+// without holding them in registers, so the gathers' latency overlaps the
+// adds.  Each ring slot holds a neighbour's `batch` color bytes (hdr bytes,
+// 16-byte aligned) and then its whole interleaved row (ld_in * batch entries).
+// Neighbour ids are read 32 at a time, one chunk ahead.  Same summation order
+// as k_spmm's direct form.  batch >= 4 (the color bytes are one 4-, 8- or
+// 16-byte copy, or two for 32 colorings).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kBlock) k_spmm_ring(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int batch, int k,
+    const T* __restrict__ Min, int w_in, int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ tab, const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = ld_out * batch;
+  const int hdr = batch < 16 ? 16 : batch;                          // color bytes, padded
+  const int row_bytes = ld_in * batch * (int)sizeof(T);             // a multiple of 16
+  const int slot_bytes = hdr + row_bytes;
+  const int warp_bytes = ((acc_len * (int)sizeof(T) + 15) & ~15) + R * slot_bytes;
+  unsigned char* wbase = sm_raw + (int64_t)warp * warp_bytes;
+  T* acc = reinterpret_cast<T*>(wbase);
+  unsigned char* ring = wbase + ((acc_len * (int)sizeof(T) + 15) & ~15);
+  const int L = 32 / batch;
+  const int b = lane & (batch - 1), jl = lane / batch;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int n16 = row_bytes >> 4;
+  const int64_t ld_out_row = (int64_t)batch * ld_out;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  const unsigned char* Mb = reinterpret_cast<const unsigned char*>(Min);
+  // issue the copies of neighbour u into ring slot `sl` (all lanes take part)
+  auto issue = [&](int sl, int32_t u) {
+    unsigned char* dst = ring + sl * slot_bytes;
+    const unsigned char* crow = colors + (int64_t)u * batch;
+    if (lane == 0) {
+      if (batch == 4) cp_async_small<4>(dst, crow);
+      else if (batch == 8) cp_async_small<8>(dst, crow);
+      else cp_async16(dst, crow);
+    } else if (lane == 1 && batch == 32) {
+      cp_async16(dst + 16, crow + 16);
+    }
+    const unsigned char* src = Mb + (int64_t)u * row_bytes;
+    for (int c = lane; c < n16; c += 32) cp_async16(dst + hdr + c * 16, src + c * 16);
+  };
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = (int)((color_word(colors, it.row, batch, word) >> shift) & 0xffu) * k;
+    const int deg = it.hi - it.lo;
+    int32_t ids_cur = lane < deg ? __ldg(col_idx + it.lo + lane) : 0;
+    int32_t ids_nxt = 32 + lane < deg ? __ldg(col_idx + it.lo + 32 + lane) : 0;
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const int32_t u = __shfl_sync(0xffffffffu, ids_cur, s);
+      if (s < deg) issue(s, u);
+      cp_async_commit();
+    }
+    for (int i = 0; i < deg; ++i) {
+      if (i > 0 && (i & 31) == 0) {  // next chunk of neighbour ids
+        ids_cur = ids_nxt;
+        ids_nxt = i + 32 + lane < deg ? __ldg(col_idx + it.lo + i + 32 + lane) : 0;
+      }
+      cp_async_wait<R - 1>();
+      __syncwarp();
+      const unsigned char* slot = ring + (i % R) * slot_bytes;
+      const int cu = slot[b];
+      const T* row = reinterpret_cast<const T*>(slot + hdr);
+      const uint32_t* pt = tab + (int64_t)(cvk + cu) * w_in + jl;
+      int q = 0;
+      for (; q + 4 <= ns; q += 4) {
+        const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)];
+        const uint32_t p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
+        const T x0 = row[lane + 32 * q], x1 = row[lane + 32 * (q + 1)];
+        const T x2 = row[lane + 32 * (q + 2)], x3 = row[lane + 32 * (q + 3)];
+        if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += x0;
+        if (p1 < (uint32_t)ld_out) acc[p1 * batch + b] += x1;
+        if (p2 < (uint32_t)ld_out) acc[p2 * batch + b] += x2;
+        if (p3 < (uint32_t)ld_out) acc[p3 * batch + b] += x3;
+      }
+      for (; q < ns; ++q) {
+        const uint32_t p0 = pt[L * q];
+        if (p0 < (uint32_t)ld_out) acc[p0 * batch + b] += row[lane + 32 * q];
+      }
+      __syncwarp();  // every lane is done with this slot before it is refilled
+      const int nx = i + R;  // the neighbour whose row goes into this slot next
+      const int32_t u = __shfl_sync(0xffffffffu, (nx & ~31) == (i & ~31) ? ids_cur : ids_nxt, nx & 31);
+      if (nx < deg) issue(i % R, u);
+      cp_async_commit();
+    }
+    T* dst = it.heavy ? scratch + item * ld_out_row : P + (int64_t)it.row * ld_out_row;
+    __syncwarp();
+    for (int i = lane; i < acc_len; i += 32) {
+      const T x = acc[i];
+      dst[i] = x;
+      if (!it.heavy) m = fmaxf(m, (float)x);
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
+// Register-bucket form, for passes of one coloring (batch 1).  All 32 lanes of
+// a warp work on the same row and coloring, so a neighbour's color c(u) is the
+// same for the whole warp: its row entries are added to the register bucket
+// Q[c(u)] through a warp-uniform switch - no index lookup and no shared-memory
+// traffic per neighbour, only the coalesced gather.  A row's w_in columns are
+// split over `wpr` warps of 32 * NS columns; the buckets are then flushed to
+// shared memory and P(v, S) = sum over the colors c of S of Q[c][S - c]
+// resolved through inv_tab[c(v)][S] as in the bucketed form.  Neighbours are
+// added in CSR order (fixed FP32 summation order).
+#define SGC_RB_CASE(C)                               \
+  case C:                                            \
+    _Pragma("unroll") for (int q = 0; q < NS; ++q) { \
+      acc[C][q] += x[i][q];                          \
+    }                                                \
+    break;
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kBlock) k_spmm_rb(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, int p, const T* __restrict__ Min,
+    int w_in, int ld_in, T* __restrict__ P, int w_out, int ld_out, T* __restrict__ scratch,
+    const uint32_t* __restrict__ inv_tab, int wpr, const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int UNR = 4;  // neighbours whose loads are in flight together
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = (blockDim.x >> 5) / wpr;  // row slots per block
+  const int slot = warp / wpr, slice = warp - slot * wpr;
+  const int qlen = k * w_in;
+  T* Qs = reinterpret_cast<T*>(sm_raw) + (int64_t)slot * qlen;
+  const int j0 = slice * 32 * NS + lane;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t base = (int64_t)blockIdx.x * rows; base < nitems; base += (int64_t)gridDim.x * rows) {
+    const int64_t item = base + slot;
+    const bool valid = item < nitems;
+    SpmmItem it{0, 0, 0, false};
+    int cv = 0;
+    if (valid) {
+      it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+      cv = __ldg(colors + it.row);
+      T acc[16][NS];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc[c][q] = T(0);
+      for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+        const int cnt = min(32, it.hi - e0);
+        const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+        const int c_lane = lane < cnt ? (int)__ldg(colors + u_lane) : cv;
+        for (int t = 0; t < cnt; t += UNR) {
+          T x[UNR][NS];
+          int cu[UNR];
+#pragma unroll
+          for (int i = 0; i < UNR; ++i) {
+            const int tt = t + i;
+            const int32_t u = __shfl_sync(0xffffffffu, u_lane, tt & 31);
+            cu[i] = __shfl_sync(0xffffffffu, c_lane, tt & 31);
+            if (tt >= cnt) cu[i] = cv;  // past the chunk: contributes nothing
+            const T* src = Min + (int64_t)u * ld_in;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+              const int j = j0 + 32 * q;
+              x[i][q] = (tt < cnt && j < w_in) ? __ldg(src + j) : T(0);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < UNR; ++i) {
+            if (cu[i] == cv) continue;  // a neighbour of v's own color never contributes
+            switch (cu[i]) {
+              SGC_RB_CASE(0) SGC_RB_CASE(1) SGC_RB_CASE(2) SGC_RB_CASE(3)
+              SGC_RB_CASE(4) SGC_RB_CASE(5) SGC_RB_CASE(6) SGC_RB_CASE(7)
+              SGC_RB_CASE(8) SGC_RB_CASE(9) SGC_RB_CASE(10) SGC_RB_CASE(11)
+              SGC_RB_CASE(12) SGC_RB_CASE(13) SGC_RB_CASE(14) SGC_RB_CASE(15)
+              default: break;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < k) {
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            const int j = j0 + 32 * q;
+            if (j < w_in) Qs[c * w_in + j] = acc[c][q];
+          }
+        }
+    }
+    __syncthreads();
+    if (valid) {
+      T* dst = it.heavy ? scratch + item * (int64_t)ld_out : P + (int64_t)it.row * ld_out;
+      const uint32_t* ent0 = inv_tab + (int64_t)cv * w_out * p;
+      for (int i = slice * 32 + lane; i < ld_out; i += wpr * 32) {
+        T val = T(0);
+        if (i < w_out) {
+          const uint32_t* ent = ent0 + (int64_t)i * p;
+          for (int t = 0; t < p; ++t) {
+            const uint32_t e = __ldg(ent + t);
+            const int c = (int)(e & 0xffu), j = (int)(e >> 8);
+            if (c < k && j < w_in) val += Qs[c * w_in + j];
+          }
+        }
+        dst[i] = val;
+        if (!it.heavy) m = fmaxf(m, (float)val);
+      }
+    }
+    __syncthreads();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+#undef SGC_RB_CASE
 
 // heavy rows: P(h, :) = sum of the row's segment partials, in segment order
 template <typename T>
@@ -642,16 +1099,16 @@ int grid_for(int64_t work, int per_block, int cap) {
   return (int)g;
 }
 
-template <typename T, bool BUCKETS, int NSMAX>
+template <typename T, bool BUCKETS, int NSMAX, int PT = 0>
 void launch_spmm_k(const sgc_graph* g, const PlanOp& op, int batch, int k, const uint8_t* colors, const T* M, T* P,
                    T* scratch, const uint32_t* tab, int tab_smem, const ScaleState* si, ScaleState* so, int wpb,
-                   size_t smem, cudaStream_t st) {
-  allow_smem(k_spmm<T, BUCKETS, NSMAX>, smem);
+                   size_t smem, cudaStream_t st, int tab_ld = 0, int grid_cap = 1 << 30) {
+  allow_smem(k_spmm<T, BUCKETS, NSMAX, PT>, smem);
   const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
-  k_spmm<T, BUCKETS, NSMAX><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(
+  k_spmm<T, BUCKETS, NSMAX, PT><<<grid_for(nitems, wpb, grid_cap), 32 * wpb, smem, st>>>(
       g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, colors,
       batch, k, op.p, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab, tab_smem,
-      si, so);
+      tab_ld > 0 ? tab_ld : (int)op.cols_p, si, so);
 }
 
 // Launch shape of the SpMM: the direct form keeps a plain loop (few registers,
@@ -660,19 +1117,68 @@ template <typename T>
 sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, const uint8_t* colors, const T* M,
                        T* P, T* scratch, const uint32_t* tab, const ScaleState* si, ScaleState* so, int num_sms,
                        size_t smem_cap, cudaStream_t st, int64_t* nk) {
+  if (op.spmm_buckets && op.spmm_variant == 2) {
+    // register buckets: one coloring per pass; wpr warps of 32 * NS columns per row
+    if (batch != 1) return fail(SGC_ERR_INTERNAL, "register-bucket SpMM needs one coloring per pass");
+    const int w_in = (int)op.cols_p;
+    const int ns = w_in <= 32 ? 1 : w_in <= 512 ? 2 : 4;
+    const int wpr = (w_in + 32 * ns - 1) / (32 * ns);
+    if (wpr > kBlock / 32 || k > 16) return fail(SGC_ERR_UNSUPPORTED, "SpMM row too wide for register buckets");
+    const int rows = (kBlock / 32) / wpr;
+    const size_t smem_rb = (size_t)rows * k * w_in * sizeof(T);
+    if (smem_rb > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "register-bucket rows do not fit in shared memory");
+    const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+    const int threads = rows * wpr * 32;
+#define SGC_RB(NS_)                                                                                          \
+  do {                                                                                                       \
+    allow_smem(k_spmm_rb<T, NS_>, smem_rb);                                                                  \
+    k_spmm_rb<T, NS_><<<grid_for(nitems, rows, 1 << 30), threads, smem_rb, st>>>(                           \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
+        colors, k, op.p, M, w_in, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab, wpr, si,   \
+        so);                                                                                                 \
+  } while (0)
+    if (ns == 1) SGC_RB(1);
+    else if (ns == 2) SGC_RB(2);
+    else SGC_RB(4);
+#undef SGC_RB
+    ++*nk;
+    if (g->n_heavy > 0) {
+      constexpr int VN = Vec16<T>::n;
+      k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * (op.ld_out / VN), kBlock, 16 * num_sms), kBlock, 0, st>>>(
+          g->d_heavy_seg, g->n_heavy, scratch, op.ld_out, P, op.ld_out, so);
+      ++*nk;
+    }
+    return SGC_OK;
+  }
   const size_t per_warp = op.spmm_buckets ? (size_t)spmm_bucket_bytes(batch, k, op.cols_p, (int)sizeof(T))
                                           : (size_t)batch * op.ld_out * sizeof(T);
   // the bucketed form's resolve table is staged in shared memory when small;
   // the direct form reads its position table through L1 (staging it in shared
   // memory measured slower: bank conflicts on the scattered lookups)
   const int64_t tab_words = (int64_t)k * op.cols_out * op.p;
-  const int tab_smem = op.spmm_buckets && tab_words * 4 <= 16 * 1024 ? (int)tab_words : 0;
+  const int pos_bytes = op.spmm_buckets ? 0 : op.spmm_pos_bytes;
+  const int64_t packed_ld = pos_bytes ? spmm_packed_ld(op.cols_p, pos_bytes) : 0;
+  const int tab_smem = pos_bytes ? (int)(((int64_t)k * k * packed_ld * pos_bytes + 3) / 4)
+                       : op.spmm_buckets && tab_words * 4 <= 16 * 1024 ? (int)tab_words
+                                                                        : 0;
   int wpb = kBlock / 32;
   while (wpb > 1 && per_warp * wpb + (size_t)tab_smem * 4 > smem_cap) wpb /= 2;
   if (per_warp * wpb + (size_t)tab_smem * 4 > smem_cap)
     return fail(SGC_ERR_UNSUPPORTED, "SpMM row does not fit in shared memory");
   const size_t smem = per_warp * wpb + (size_t)tab_smem * 4;
-  if (op.spmm_buckets) {
+  if (op.spmm_buckets && op.spmm_variant == 7) {
+    const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+#define SGC_BK(B_)                                                                                             do {                                                                                                           allow_smem(k_spmm_bk<T, B_>, smem);                                                                          k_spmm_bk<T, B_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                                       g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,         colors, k, op.p, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab,         tab_smem, si, so);                                                                                     } while (0)
+    switch (batch) {
+      case 1: SGC_BK(1); break;
+      case 2: SGC_BK(2); break;
+      case 4: SGC_BK(4); break;
+      case 8: SGC_BK(8); break;
+      case 16: SGC_BK(16); break;
+      default: SGC_BK(32); break;
+    }
+#undef SGC_BK
+  } else if (op.spmm_buckets) {
     const int64_t per_lane = (op.cols_p + 32 / batch - 1) / (32 / batch);
     if (per_lane <= 4)
       launch_spmm_k<T, true, 4>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);
@@ -693,7 +1199,55 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
   } while (0)
-    if (variant == 1 && per_lane <= 4) SGC_DIRECT_PF(4);
+    if (variant == 5 || variant == 6) {
+#define SGC_D(B_, LM_)                                                                                       \
+  do {                                                                                                       \
+    allow_smem(k_spmm_d<T, B_, LM_>, smem);                                                                  \
+    k_spmm_d<T, B_, LM_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                           \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
+        colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, nsp, si, so);         \
+  } while (0)
+#define SGC_D2(B_)                 \
+  do {                             \
+    if (variant == 6)              \
+      SGC_D(B_, true);             \
+    else                           \
+      SGC_D(B_, false);            \
+  } while (0)
+      const int nsp = (int)spmm_lane_nsp(op.cols_p, 32 / batch);
+      switch (batch) {
+        case 1: SGC_D2(1); break;
+        case 2: SGC_D2(2); break;
+        case 4: SGC_D2(4); break;
+        case 8: SGC_D2(8); break;
+        case 16: SGC_D2(16); break;
+        default: SGC_D2(32); break;
+      }
+#undef SGC_D2
+#undef SGC_D
+    } else if (variant >= 3 && batch >= 4) {
+      // asynchronous-copy ring of R = 2 (variant 3) or 4 (variant 4) neighbour rows per warp
+      const int R = variant == 3 ? 2 : 4;
+      const size_t acc_b = ((size_t)batch * op.ld_out * sizeof(T) + 15) & ~(size_t)15;
+      const size_t slot_b = (size_t)(batch < 16 ? 16 : batch) + (size_t)op.ld_p * batch * sizeof(T);
+      const size_t per_warp_ring = acc_b + R * slot_b;
+      int wr = kBlock / 32;
+      while (wr > 1 && per_warp_ring * wr > smem_cap) wr /= 2;
+      if (per_warp_ring * wr > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "SpMM ring does not fit in shared memory");
+      const size_t smem_r = per_warp_ring * wr;
+#define SGC_RING(R_)                                                                                           do {                                                                                                           allow_smem(k_spmm_ring<T, R_>, smem_r);                                                                      k_spmm_ring<T, R_><<<grid_for(nitems, wr, 1 << 30), 32 * wr, smem_r, st>>>(                                     g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);         } while (0)
+      if (R == 2) SGC_RING(2);
+      else SGC_RING(4);
+#undef SGC_RING
+    } else
+    // a staged table is loaded once per block: a grid of a few blocks per SM, each striding over the rows
+    if (pos_bytes == 1)
+      launch_spmm_k<T, false, 0, 1>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st,
+                                    (int)packed_ld, 16 * num_sms);
+    else if (pos_bytes == 2)
+      launch_spmm_k<T, false, 0, 2>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st,
+                                    (int)packed_ld, 16 * num_sms);
+    else if (variant == 1 && per_lane <= 4) SGC_DIRECT_PF(4);
     else if (variant == 1 && per_lane <= 8) SGC_DIRECT_PF(8);
     else if (variant == 1 && per_lane <= 12) SGC_DIRECT_PF(12);
     else launch_spmm_k<T, false, 0>(g, op, batch, k, colors, M, P, scratch, tab, tab_smem, si, so, wpb, smem, st);

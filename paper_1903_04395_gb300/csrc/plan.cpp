@@ -254,6 +254,22 @@ void ema_shape(int64_t ca, int64_t cp, int elem, int smem_cap, int* rows, int* r
 
 }  // namespace
 
+// Where entry j of a neighbour u's row lands in v's SpMM output row (relative
+// colors, Eq. 1 ranks), for c(v) = cv and c(u) = cu; all ones when nowhere.
+static uint32_t spmm_position(const ColorIndex& cr, int k, int p, int cv, int cu, uint64_t j) {
+  if (cu == cv) return 0xFFFFFFFFu;
+  const int K = k - 1;
+  const uint32_t rel_u = cr.unrank_mask(j, p - 1);
+  uint32_t abs_set = 1u << cu;
+  for (int x = 0; x < K; ++x)
+    if (rel_u >> x & 1u) abs_set |= 1u << (x < cu ? x : x + 1);
+  if (abs_set >> cv & 1u) return 0xFFFFFFFFu;
+  uint32_t rel_v = 0;
+  for (int y = 0; y < k; ++y)
+    if (abs_set >> y & 1u) rel_v |= 1u << (y < cv ? y : y - 1);
+  return cr.rank_mask(rel_v);
+}
+
 // Index tables.  All count tables are stored in relative-color form (see
 // make_plan): a row of vertex v is indexed by subsets of the K = k-1 colors
 // other than c(v), relabelled 0..K-1 by skipping c(v), and ranked by Eq. 1
@@ -276,22 +292,43 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
     const uint64_t w_in = cr.nsets(p - 1);
     for (int cv = 0; cv < k; ++cv)
       for (int cu = 0; cu < k; ++cu)
+        for (uint64_t j = 0; j < w_in; ++j) tabs->push_back(spmm_position(cr, k, p, cv, cu, j));
+  } else if (kind == OP_SPMM + 400) {
+    // the same positions in 16-bit entries, lane-major for a = L lanes per coloring:
+    // row [c_v][c_u] holds, for each lane jl < L, the entries j = jl + L q (q < nsp,
+    // spmm_lane_nsp, padding all ones) contiguously, so a lane reads four at once
+    const int p = t, L = a;
+    const uint64_t w_in = cr.nsets(p - 1);
+    const int64_t nsp = spmm_lane_nsp((int64_t)w_in, L);
+    std::vector<uint16_t> h((size_t)(k * k * L * nsp), 0xFFFFu);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
         for (uint64_t j = 0; j < w_in; ++j) {
-          uint32_t out = 0xFFFFFFFFu;
-          if (cu != cv) {
-            const uint32_t rel_u = cr.unrank_mask(j, p - 1);
-            uint32_t abs_set = 1u << cu;
-            for (int x = 0; x < K; ++x)
-              if (rel_u >> x & 1u) abs_set |= 1u << (x < cu ? x : x + 1);
-            if (!(abs_set >> cv & 1u)) {
-              uint32_t rel_v = 0;
-              for (int y = 0; y < k; ++y)
-                if (abs_set >> y & 1u) rel_v |= 1u << (y < cv ? y : y - 1);
-              out = cr.rank_mask(rel_v);
-            }
-          }
-          tabs->push_back(out);
+          const uint32_t pos = spmm_position(cr, k, p, cv, cu, j);
+          if (pos == 0xFFFFFFFFu) continue;
+          const int64_t jl = (int64_t)j % L, q = (int64_t)j / L;
+          h[(size_t)(((int64_t)(cv * k + cu) * L + jl) * nsp + q)] = (uint16_t)pos;
         }
+    for (size_t i = 0; i < h.size(); i += 2) tabs->push_back((uint32_t)h[i] | (uint32_t)h[i + 1] << 16);
+  } else if (kind == OP_SPMM + 300) {
+    // the same positions packed into a-byte entries (a = 1 or 2; all ones = nowhere)
+    // for a table staged in shared memory: rows [c_v][c_u] of spmm_packed_ld entries
+    const int p = t, eb = a;
+    const uint64_t w_in = cr.nsets(p - 1);
+    const int64_t ld = spmm_packed_ld((int64_t)w_in, eb);
+    std::vector<uint8_t> bytes((size_t)(k * k * ld * eb), 0xFF);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
+        for (uint64_t j = 0; j < w_in; ++j) {
+          const uint32_t pos = spmm_position(cr, k, p, cv, cu, j);
+          if (pos == 0xFFFFFFFFu) continue;
+          const size_t at = (size_t)(((int64_t)(cv * k + cu) * ld + (int64_t)j) * eb);
+          bytes[at] = (uint8_t)(pos & 0xffu);
+          if (eb == 2) bytes[at + 1] = (uint8_t)(pos >> 8);
+        }
+    for (size_t i = 0; i < bytes.size(); i += 4)
+      tabs->push_back((uint32_t)bytes[i] | (uint32_t)bytes[i + 1] << 8 | (uint32_t)bytes[i + 2] << 16 |
+                      (uint32_t)bytes[i + 3] << 24);
   } else if (kind == OP_SPMM + 100) {
     // bucketed SpMM: [c_v][S][t] for the p-subsets S of v's relative colors and the
     // t-th (ascending) element of S: its absolute color c | (the index, relative to c,
@@ -402,13 +439,15 @@ static void use_buf(Plan* P, int buf, int op) {
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
 }
 
-// Direct SpMM loop used when no tuned shape says otherwise: 0 = chunked (the
-// default), 1 = next-neighbour prefetch (measured equal on R-MAT 20 with more
-// registers); SGC_SPMM_DIRECT overrides.
+// Direct SpMM loop used when no tuned shape says otherwise: 5 = specialised for
+// the batch (the default: 20-30% faster than the others on R-MAT 20), 0 =
+// chunked with a runtime batch, 1 = next-neighbour prefetch; SGC_SPMM_DIRECT
+// overrides.
 static int default_spmm_variant() {
   static const int v = [] {
     const char* e = std::getenv("SGC_SPMM_DIRECT");
-    return e ? std::atoi(e) : 0;
+    const int x = e ? std::atoi(e) : 5;
+    return x == 0 || x == 1 ? x : 5;
   }();
   return v;
 }
@@ -416,6 +455,28 @@ static int default_spmm_variant() {
 // Bucketed SpMM rows the autotuner may try (the planner's own limit is
 // kSpmmBucketMaxBytes): up to 24 KB per warp still keeps 9 warps per SM.
 constexpr int64_t kSpmmBucketTuneMaxBytes = 24 * 1024;
+
+// The register-bucket SpMM (one coloring per pass): a row's w_in columns over
+// at most 8 warps of 32, 64 or 128 columns, k <= 16 buckets in registers, and
+// the rows of a block's buckets in shared memory.
+static bool reg_buckets_fit(int batch, int k, int64_t w_in, int elem, const sgc_graph* g) {
+  if (batch != 1 || k > 16 || w_in > 1024) return false;
+  const int64_t ns = w_in <= 32 ? 1 : w_in <= 512 ? 2 : 4;
+  const int64_t wpr = (w_in + 32 * ns - 1) / (32 * ns);
+  const int64_t rows = 8 / wpr;
+  const int64_t smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
+  return rows * k * w_in * elem <= smem_cap;
+}
+
+// Bytes of the direct form's packed position table (entries of 1 byte when
+// every position and the all-ones marker fit, else 2), or 0 when it is too
+// large to stage in shared memory beside the accumulators.
+static int64_t spmm_packed_bytes(int k, int64_t w_in, int64_t ld_out) {
+  if (ld_out >= 65535) return 0;
+  const int eb = ld_out < 255 ? 1 : 2;
+  const int64_t bytes = (int64_t)k * k * spmm_packed_ld(w_in, eb) * eb;
+  return bytes <= kSpmmPackedMaxBytes ? bytes : 0;
+}
 
 static int64_t spmm_cols_per_lane(int batch, int64_t cols_p) {
   const int lanes_per_col = 32 / batch;
@@ -505,22 +566,55 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.ld_p = table_ld[C.p];
         op.state_p = table_state[C.p];
         op.spmm_buckets = spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketMaxBytes;
-        op.spmm_variant = op.spmm_buckets ? 0 : default_spmm_variant();
+        op.spmm_variant = op.spmm_buckets ? 7 : default_spmm_variant();
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
         if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
           op.spmm_buckets = true;
           op.spmm_variant = 0;
-        } else if (shape == kShapeSpmmDirect) {
+        } else if (shape == kShapeSpmmBucketsB &&
+                   spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
+          op.spmm_buckets = true;
+          op.spmm_variant = 7;
+        } else if (shape == kShapeSpmmDirect) {  // the chunked loop with a runtime batch
           op.spmm_buckets = false;
           op.spmm_variant = 0;
         } else if (shape == kShapeSpmmPrefetch && spmm_cols_per_lane(batch, op.cols_p) <= 12) {
           op.spmm_buckets = false;
           op.spmm_variant = 1;
+        } else if (shape == kShapeSpmmRegBuckets && reg_buckets_fit(batch, k, op.cols_p, elem, g)) {
+          op.spmm_buckets = true;
+          op.spmm_variant = 2;
+        } else if (shape == kShapeSpmmDirectB) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 5;
+        } else if (shape == kShapeSpmmDirectBLane && op.ld_out < 65535) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 6;
+        } else if ((shape == kShapeSpmmRing2 || shape == kShapeSpmmRing4) && batch >= 4) {
+          op.spmm_buckets = false;
+          op.spmm_variant = shape == kShapeSpmmRing2 ? 3 : 4;
+        } else if (shape == kShapeSpmmPacked && spmm_packed_bytes(k, op.cols_p, op.ld_out) > 0) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 0;
+          op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_buckets ? kShapeSpmmBuckets : op.spmm_variant ? kShapeSpmmPrefetch : kShapeSpmmDirect;
-        op.tab_off = build_tabs ? build_table(cr, k, op.spmm_buckets ? (OpKind)(OP_SPMM + 100) : OP_SPMM, Pc.size,
-                                              0, &P->tabs, &tcache)
-                                : 0;
+        op.shape = op.spmm_variant == 7  ? kShapeSpmmBucketsB
+                   : op.spmm_variant == 6  ? kShapeSpmmDirectBLane
+                   : op.spmm_variant == 5  ? kShapeSpmmDirectB
+                   : op.spmm_variant == 3  ? kShapeSpmmRing2
+                   : op.spmm_variant == 4  ? kShapeSpmmRing4
+                   : op.spmm_variant == 2  ? kShapeSpmmRegBuckets
+                   : op.spmm_buckets     ? kShapeSpmmBuckets
+                   : op.spmm_pos_bytes   ? kShapeSpmmPacked
+                   : op.spmm_variant     ? kShapeSpmmPrefetch
+                                         : kShapeSpmmDirect;
+        op.tab_off = !build_tabs             ? 0
+                     : op.spmm_variant == 6  ? build_table(cr, k, (OpKind)(OP_SPMM + 400), Pc.size, 32 / batch,
+                                                           &P->tabs, &tcache)
+                     : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs, &tcache)
+                     : op.spmm_pos_bytes   ? build_table(cr, k, (OpKind)(OP_SPMM + 300), Pc.size, op.spmm_pos_bytes,
+                                                         &P->tabs, &tcache)
+                                           : build_table(cr, k, OP_SPMM, Pc.size, 0, &P->tabs, &tcache);
         max_spmm_width = std::max<int64_t>(max_spmm_width, op.ld_out * batch);
         op.alg_bytes = 4 * (nv + 1 + nnz) + nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
         double by = nnz * 4 + (double)elem * nv * (double)(op.cols_p + op.cols_out);
@@ -629,7 +723,25 @@ static bool tables_in_range(const Plan& P, int k) {
     if (op.tab_off < 0 || P.tabs.empty()) continue;
     const uint32_t* t = P.tabs.data() + op.tab_off;
     const int64_t left = (int64_t)P.tabs.size() - op.tab_off;
-    if (op.kind == OP_SPMM && !op.spmm_buckets) {
+    if (op.kind == OP_SPMM && op.spmm_variant == 6) {
+      const int L = 32 / P.batch;
+      const int64_t n = (int64_t)k * k * L * spmm_lane_nsp(op.cols_p, L);
+      if ((n + 1) / 2 > left) return false;
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
+      for (int64_t i = 0; i < n; ++i)
+        if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
+    } else if (op.kind == OP_SPMM && op.spmm_pos_bytes > 0) {
+      const int eb = op.spmm_pos_bytes;
+      const int64_t ld = spmm_packed_ld(op.cols_p, eb);
+      const int64_t nbytes = (int64_t)k * k * ld * eb;
+      if ((nbytes + 3) / 4 > left) return false;
+      const uint8_t* b = reinterpret_cast<const uint8_t*>(t);
+      const uint32_t none = eb == 1 ? 0xFFu : 0xFFFFu;
+      for (int64_t i = 0; i < nbytes; i += eb) {
+        const uint32_t v = eb == 1 ? b[i] : (uint32_t)b[i] | (uint32_t)b[i + 1] << 8;
+        if (v != none && v >= (uint32_t)op.cols_out) return false;
+      }
+    } else if (op.kind == OP_SPMM && !op.spmm_buckets) {
       const int64_t n = (int64_t)k * k * op.cols_p;
       if (n > left) return false;
       for (int64_t i = 0; i < n; ++i)
@@ -660,8 +772,19 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
   const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
   if (op.kind == OP_SPMM) {
     c.push_back(kShapeSpmmDirect);
+    c.push_back(kShapeSpmmDirectB);
+    if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
     if (spmm_cols_per_lane(P.batch, op.cols_p) <= 12) c.push_back(kShapeSpmmPrefetch);
-    if (spmm_bucket_bytes(P.batch, P.k, op.cols_p, P.elem) <= kSpmmBucketTuneMaxBytes) c.push_back(kShapeSpmmBuckets);
+    if (spmm_bucket_bytes(P.batch, P.k, op.cols_p, P.elem) <= kSpmmBucketTuneMaxBytes) {
+      c.push_back(kShapeSpmmBuckets);
+      c.push_back(kShapeSpmmBucketsB);
+    }
+    if (reg_buckets_fit(P.batch, P.k, op.cols_p, P.elem, g)) c.push_back(kShapeSpmmRegBuckets);
+    if (spmm_packed_bytes(P.k, op.cols_p, op.ld_out) > 0) c.push_back(kShapeSpmmPacked);
+    if (P.batch >= 4) {
+      c.push_back(kShapeSpmmRing2);
+      c.push_back(kShapeSpmmRing4);
+    }
   } else if (op.kind == OP_EMA) {
     for (int r : {64, 32, 16, 8})
       if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap) c.push_back(r);

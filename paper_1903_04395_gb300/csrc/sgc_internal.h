@@ -148,7 +148,13 @@ struct PlanOp {
   int64_t cols_p = 0, ld_p = 0;
   int64_t nsplit = 0;        // binom(t, p)
   bool spmm_buckets = false; // SpMM: sum neighbour rows per neighbour color, resolve once per row
-  int spmm_variant = 0;      // direct SpMM loop: 0 chunked, 1 next-neighbour prefetch
+  int spmm_variant = 0;      // direct SpMM loop: 0 chunked, 1 next-neighbour prefetch, 3 / 4 ring
+                             // of 2 / 4 asynchronous row copies, 5 / 6 compile-time batch with
+                             // the 32-bit / lane-major 16-bit position table;
+                             // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
+                             // memory buckets with a compile-time batch
+  int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
+                             // packed entries staged in shared memory
   int shape = 0;             // launch shape code (kSpmm* / eMA rows), see op_shape_candidates
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_rpl = 1;           // eMA: rows per lane
@@ -179,10 +185,26 @@ struct Plan {
   int64_t scratch_width = 0;
 };
 
-// Launch-shape codes an autotuner may pick per op (0 keeps the planner's choice).
+// Launch-shape codes an autotuner may pick per op (0 keeps the planner's choice);
+// eMA: the rows a block stages.
 // SpMM: the direct form with its chunked loop, the direct form with a
-// next-neighbour prefetch, or the bucketed form; eMA: the rows a block stages.
-constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3;
+// next-neighbour prefetch, the bucketed form (buckets in shared memory),
+// register buckets (one coloring per pass), or the direct form with its
+// position table packed into 1- or 2-byte entries and staged in shared memory.
+// The direct form can also stream neighbour rows through a ring of 2 or 4
+// shared-memory slots filled by asynchronous copies (batch >= 4), or run with
+// the batch as a compile-time constant (immediate offsets, shuffled ids) with
+// the 32-bit position table or a lane-major 16-bit one; likewise the
+// bucketed form (10).
+constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3, kShapeSpmmRegBuckets = 4,
+              kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
+              kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10;
+constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
+// entries per lane of the lane-major position table of the batch-specialised
+// direct form (L lanes per coloring; a multiple of 4 so a lane reads 4 at once)
+inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }
+// entries per [c_v][c_u] row of the packed position table (rows of whole words)
+inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4 * 4 / eb; }
 
 // Plan the DP for template t on graph g.  root < 0 and policy < 0 let the
 // cost model choose; batch is the number of colorings per pass.  Index tables

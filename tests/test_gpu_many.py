@@ -92,16 +92,19 @@ def test_recorded_sequence_replays_with_new_seeds(er_graph):
     assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
 
 
-@pytest.mark.parametrize("spmm_shape", [1, 2, 3])
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_spmm_shape(precision, spmm_shape):
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=3)
     g = sgc.Graph(rp, ci)
-    for parent in (sgcgen.pruefer_tree(8, 1008), sgcgen.spider_tree([3, 3, 3])):
+    assert g.stats()["n_heavy"] > 0  # rows split into segments are covered
+    # register buckets take one coloring per pass
+    batch = 1 if spmm_shape == 4 else 0
+    for parent in (sgcgen.pruefer_tree(8, 1008), sgcgen.spider_tree([3, 3, 3]), sgcgen.pruefer_tree(13, 7)):
         t = sgc.Template(parent)
-        seeds = np.arange(1, 12, dtype=np.uint64)  # 8 + 2 + 1
-        r = sgc.count(g, t, seeds, precision=precision, spmm_shape=spmm_shape)
+        seeds = np.arange(1, 12 if len(parent) < 13 else 3, dtype=np.uint64)  # 8 + 2 + 1
+        r = sgc.count(g, t, seeds, precision=precision, spmm_shape=spmm_shape, batch=batch)
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
