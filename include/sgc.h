@@ -81,11 +81,14 @@ typedef struct sgc_options {
                           batch = 1), 5 direct with a packed position table in shared memory,
                           6 / 7 direct with neighbour rows streamed through a ring of 2 / 4
                           asynchronous copies (batch >= 4), 8 / 9 direct specialised for the
-                          batch (9: with a lane-major 16-bit position table), 10 bucketed
-                          specialised for the batch; ops it does not fit keep theirs.  0 (default) = planner or
+                          batch (9: with a lane-major 16-bit position table; 11 / 12: with 8 / 12
+                          entries per lane in flight), 10 bucketed specialised for the batch;
+                          ops it does not fit keep theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
-  int32_t ema_rows;    /* force the rows an eMA block stages: 64, 32, 16, 8 or 4 (ops whose rows do
-                          not fit in shared memory keep theirs); 0 (default) = planner or autotuner */
+  int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8 or 4 rows staged column-major per
+                          block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
+                          1 / 2 rows per lane (4..32 colorings per pass); ops it does not fit keep
+                          theirs; 0 (default) = planner or autotuner */
 } sgc_options;
 
 /* Fill *opt with the defaults described above. */
@@ -226,8 +229,9 @@ typedef struct sgc_tune_entry {
   int32_t chosen;            /* index of the kept shape in shapes[] */
   int32_t shapes[8];         /* SpMM: 1 direct, 2 direct with prefetch, 3 bucketed, 4 register buckets,
                                 5 direct with packed positions, 6 / 7 direct with a copy ring,
-                                8 / 9 direct specialised for the batch, 10 bucketed specialised;
-                                eMA: rows staged per block */
+                                8 / 9 / 11 / 12 direct specialised for the batch, 10 bucketed
+                                specialised;
+                                eMA: rows staged per block, or 101 / 102 vertex tiles */
   double ms[8];              /* device time of the op, one pass, per shape */
 } sgc_tune_entry;
 

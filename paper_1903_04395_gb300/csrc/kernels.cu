@@ -478,10 +478,11 @@ __global__ void __launch_bounds__(kBlock) k_spmm_direct_pf(
 // lane-major with 16-bit entries (tab16[c_v][c_u][jl][q], nsp entries per
 // lane, all ones = nowhere), from which a lane reads four positions with one
 // 8-byte load (LM = true; faster for some widths and batches, slower for
-// others: the autotuner picks).  Neighbour ids and their color words are read
+// others: the autotuner picks).  G > 0 issues G predicated entries per lane at
+// once (more loads in flight for wide rows); G = 0 takes four at a time.  Neighbour ids and their color words are read
 // 32 at a time, one per lane, and shuffled.  Same summation order as k_spmm's
 // direct form.
-template <typename T, int B, bool LM>
+template <typename T, int B, bool LM, int G>
 __global__ void __launch_bounds__(kBlock) k_spmm_d(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
             if (p2 < (uint32_t)ld_out) acc[p2 * B + b] += x2;
             if (p3 < (uint32_t)ld_out) acc[p3 * B + b] += x3;
           }
-        } else {  // 32-bit table [c_v][c_u][j]
+        } else if (G == 0) {  // 32-bit table [c_v][c_u][j], four entries at a time
           const uint32_t* pt = tab + (cvk + cu) * w_in + jl;
           int q = 0;
           for (; q + 4 <= ns; q += 4) {
@@ -553,6 +554,22 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
             const uint32_t p0 = pt[L * q];
             const T x0 = __ldg(src + 32 * q);
             if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
+          }
+        } else {  // 32-bit table, G entries per lane in flight at once (predicated)
+          constexpr int GG = G > 0 ? G : 1;
+          const uint32_t* pt = tab + (cvk + cu) * w_in + jl;
+          for (int q = 0; q < ns; q += GG) {
+            uint32_t pp[GG];
+            T xx[GG];
+#pragma unroll
+            for (int i = 0; i < GG; ++i) {
+              const bool ok = q + i < ns;
+              pp[i] = ok ? pt[L * (q + i)] : 0xFFFFFFFFu;
+              xx[i] = ok ? __ldg(src + 32 * (q + i)) : T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < GG; ++i)
+              if (pp[i] < (uint32_t)ld_out) acc[pp[i] * B + b] += xx[i];
           }
         }
         __syncwarp();
@@ -1018,6 +1035,124 @@ __global__ void __launch_bounds__(kBlock) k_ema(
   }
 }
 
+// eMA over vertex tiles (batch B >= 4): a tile is V = (32 / B) * RPL
+// vertices, whose whole interleaved rows (all B colorings, contiguous in the
+// table) are copied into shared memory with 16-byte asynchronous copies -
+// the next tile's while the current one is combined when two buffers fit
+// (nbuf = 2).  The shared rows keep the global layout with a vertex stride
+// vs == B (mod 32), so lane l = (vertex l / B, coloring l % B) reads a
+// different bank for any column and a warp serves 32 rows of one output
+// column S.  The table holds the raw split indices (I(A), I(S \ A)); the
+// symmetric form (a table with itself) stages it once.  Same sums, in the
+// same order, as k_ema.
+template <typename T, int B, int RPL>
+__global__ void __launch_bounds__(kBlock) k_ema_v(
+    const T* __restrict__ Ma, int64_t lda, int ca, const T* __restrict__ P, int64_t ldp, int cp,
+    T* __restrict__ out, int64_t ldt, int ct, const uint2* __restrict__ tab, int nsplit, int sym, int64_t nv, int vsa,
+    int vsp, int nbuf, const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+  constexpr int VPL = 32 / B;
+  constexpr int V = VPL * RPL;
+  constexpr int LB = B == 4 ? 2 : B == 8 ? 3 : B == 16 ? 4 : 5;
+  constexpr int CH = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int b = lane & (B - 1), vl0 = lane >> LB;
+  const int buf_elems = V * vsa + (sym ? 0 : V * vsp);
+  const int vs_p = sym ? vsa : vsp;
+  float scale = sym ? 2.f : 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    const float bound = (float)(sym ? 2 * nsplit : nsplit) * state_max(st_a) * state_max(st_p);
+    s = shift_for(bound);
+    scale *= pow2f(-s);
+  }
+  const int64_t ntiles = (nv + V - 1) / V;
+  const int na = (int)(lda * B / CH), np = (int)(ldp * B / CH);  // 16-byte chunks per vertex row
+  auto issue = [&](int64_t tile, int bi) {
+    T* dA = sm + (int64_t)bi * buf_elems;
+    T* dP = dA + V * vsa;
+    const int64_t v0 = tile * V;
+    const int nvt = (int)(nv - v0 < V ? nv - v0 : V);
+    for (int i = threadIdx.x; i < nvt * na; i += blockDim.x) {
+      const int vl = i / na, c = i - vl * na;
+      cp_async16(dA + vl * vsa + c * CH, Ma + ((v0 + vl) * lda * B + (int64_t)c * CH));
+    }
+    if (!sym)
+      for (int i = threadIdx.x; i < nvt * np; i += blockDim.x) {
+        const int vl = i / np, c = i - vl * np;
+        cp_async16(dP + vl * vsp + c * CH, P + ((v0 + vl) * ldp * B + (int64_t)c * CH));
+      }
+  };
+  float m = 0.f;
+  int bi = 0;
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, 0);
+  cp_async_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    if (nbuf == 2) {
+      if (next < ntiles) issue(next, bi ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const T* A = sm + (int64_t)bi * buf_elems;
+    const T* Pp = sym ? A : A + V * vsa;
+    const int64_t v0 = tile * V;
+    for (int S = warp; S < ldt; S += nwarp) {
+      T acc[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) acc[q] = T(0);
+      if (S < ct) {
+        const uint2* tp = tab + S;
+        int j = 0;
+        for (; j + 2 <= nsplit; j += 2) {
+          const uint2 e0 = __ldg(tp), e1 = __ldg(tp + ct);
+          tp += 2 * (int64_t)ct;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int va = (vl0 + VPL * q) * vsa + b, vp = (vl0 + VPL * q) * vs_p + b;
+            acc[q] += A[va + (int)(e0.x << LB)] * Pp[vp + (int)(e0.y << LB)];
+            acc[q] += A[va + (int)(e1.x << LB)] * Pp[vp + (int)(e1.y << LB)];
+          }
+        }
+        if (j < nsplit) {
+          const uint2 e0 = __ldg(tp);
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int va = (vl0 + VPL * q) * vsa + b, vp = (vl0 + VPL * q) * vs_p + b;
+            acc[q] += A[va + (int)(e0.x << LB)] * Pp[vp + (int)(e0.y << LB)];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int64_t v = v0 + vl0 + VPL * q;
+        const T val = S < ct ? acc[q] * (T)scale : T(0);
+        if (v < nv) {
+          out[(v * ldt + S) * B + b] = val;
+          m = fmaxf(m, (float)val);
+        }
+      }
+    }
+    __syncthreads();  // every warp is done with this buffer before it is refilled
+    if (nbuf == 2) {
+      bi ^= 1;
+    } else {
+      if (next < ntiles) issue(next, 0);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait<0>();
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_a->e + st_p->e + s;
+  }
+}
+
 // ----------------------------------------------- last step + vertex sum --
 // maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p).  One thread per row
 // r = v * batch + b, rows r, r + S, ... with S (the grid's thread count) a
@@ -1199,20 +1334,24 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
   } while (0)
-    if (variant == 5 || variant == 6) {
-#define SGC_D(B_, LM_)                                                                                       \
+    if (variant == 5 || variant == 6 || variant == 8 || variant == 9) {
+#define SGC_D(B_, LM_, G_)                                                                                   \
   do {                                                                                                       \
-    allow_smem(k_spmm_d<T, B_, LM_>, smem);                                                                  \
-    k_spmm_d<T, B_, LM_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                           \
+    allow_smem(k_spmm_d<T, B_, LM_, G_>, smem);                                                              \
+    k_spmm_d<T, B_, LM_, G_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                       \
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
         colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, nsp, si, so);         \
   } while (0)
-#define SGC_D2(B_)                 \
-  do {                             \
-    if (variant == 6)              \
-      SGC_D(B_, true);             \
-    else                           \
-      SGC_D(B_, false);            \
+#define SGC_D2(B_)                   \
+  do {                               \
+    if (variant == 6)                \
+      SGC_D(B_, true, 0);            \
+    else if (variant == 8)           \
+      SGC_D(B_, false, 8);           \
+    else if (variant == 9)           \
+      SGC_D(B_, false, 12);          \
+    else                             \
+      SGC_D(B_, false, 0);           \
   } while (0)
       const int nsp = (int)spmm_lane_nsp(op.cols_p, 32 / batch);
       switch (batch) {
@@ -1275,9 +1414,49 @@ void launch_ema_r(const PlanOp& op, const T* Ma, const T* P, T* out, const uint3
       reinterpret_cast<const uint2*>(tab), (int)op.nsplit, op.ema_sym ? 1 : 0, rows, lb, sa, sp, so);
 }
 
+// vertex stride (elements) of a staged interleaved row of width ld: a multiple
+// of 16 bytes, == batch (mod 32)
+inline int ema_vstride(int64_t ld, int batch) {
+  const int x = (int)(ld * batch);
+  return x + ((batch - x % 32) % 32 + 32) % 32;
+}
+
+template <typename T, int B, int RPL>
+sgc_status launch_ema_v(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t nv,
+                        const ScaleState* sa, const ScaleState* sp, ScaleState* so, size_t smem_cap,
+                        cudaStream_t st) {
+  constexpr int V = (32 / B) * RPL;
+  const int vsa = ema_vstride(op.ld_a, B), vsp = ema_vstride(op.ld_p, B);
+  const size_t buf = ((size_t)V * vsa + (op.ema_sym ? 0 : (size_t)V * vsp)) * sizeof(T);
+  const int nbuf = 2 * buf <= smem_cap && 2 * buf <= 100 * 1024 ? 2 : 1;
+  if (buf > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "eMA vertex tile does not fit in shared memory");
+  const size_t smem = nbuf * buf;
+  allow_smem(k_ema_v<T, B, RPL>, smem);
+  const int64_t tiles = (nv + V - 1) / V;
+  k_ema_v<T, B, RPL><<<grid_for(tiles, 1, 1 << 30), kBlock, smem, st>>>(
+      Ma, op.ld_a, (int)op.cols_a, P, op.ld_p, (int)op.cols_p, out, op.ld_out, (int)op.cols_out,
+      reinterpret_cast<const uint2*>(tab), (int)op.nsplit, op.ema_sym ? 1 : 0, nv, vsa, vsp, nbuf, sa, sp, so);
+  return SGC_OK;
+}
+
 template <typename T>
 sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows, int lb,
-                      const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
+                      const ScaleState* sa, const ScaleState* sp, ScaleState* so, size_t smem_cap, cudaStream_t st) {
+  if (op.ema_vrpl > 0) {
+    const int64_t nv = rows >> lb;
+    const int B = 1 << lb;
+#define SGC_EV(B_)                                                                                \
+  return op.ema_vrpl == 2 ? launch_ema_v<T, B_, 2>(op, Ma, P, out, tab, nv, sa, sp, so, smem_cap, st) \
+                          : launch_ema_v<T, B_, 1>(op, Ma, P, out, tab, nv, sa, sp, so, smem_cap, st)
+    switch (B) {
+      case 4: SGC_EV(4);
+      case 8: SGC_EV(8);
+      case 16: SGC_EV(16);
+      case 32: SGC_EV(32);
+      default: return fail(SGC_ERR_INTERNAL, "eMA vertex tiles need 4..32 colorings per pass");
+    }
+#undef SGC_EV
+  }
   switch (op.ema_rows) {
     case 64: launch_ema_r<T, 64, 2>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
     case 32: launch_ema_r<T, 32, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
@@ -1384,7 +1563,8 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
       case OP_EMA: {
         sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
                                       reinterpret_cast<const T*>(buf(op.in_p)), reinterpret_cast<T*>(buf(op.out)),
-                                      d_tabs + op.tab_off, rows, lb, S(op.state_a), S(op.state_p), S(op.state_out), st);
+                                      d_tabs + op.tab_off, rows, lb, S(op.state_a), S(op.state_p), S(op.state_out),
+                                      smem_cap, st);
         if (rc != SGC_OK) return rc;
         ++nk;
         break;

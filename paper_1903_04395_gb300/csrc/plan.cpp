@@ -478,6 +478,15 @@ static int64_t spmm_packed_bytes(int k, int64_t w_in, int64_t ld_out) {
   return bytes <= kSpmmPackedMaxBytes ? bytes : 0;
 }
 
+// The vertex-tile eMA: batch 4..32, one buffer of (32 / batch) * rpl whole
+// vertex rows (both tables unless symmetric) in shared memory.
+static bool ema_vertex_fits(int batch, int rpl, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap) {
+  if (batch < 4 || batch > 32) return false;
+  auto vs = [&](int64_t ld) { const int64_t x = ld * batch; return x + ((batch - x % 32) % 32 + 32) % 32; };
+  const int64_t v = (32 / batch) * rpl;
+  return (v * vs(ld_a) + (sym ? 0 : v * vs(ld_p))) * elem <= smem_cap;
+}
+
 static int64_t spmm_cols_per_lane(int batch, int64_t cols_p) {
   const int lanes_per_col = 32 / batch;
   return (cols_p + lanes_per_col - 1) / lanes_per_col;
@@ -590,6 +599,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         } else if (shape == kShapeSpmmDirectBLane && op.ld_out < 65535) {
           op.spmm_buckets = false;
           op.spmm_variant = 6;
+        } else if (shape == kShapeSpmmDirectB8 || shape == kShapeSpmmDirectB12) {
+          op.spmm_buckets = false;
+          op.spmm_variant = shape == kShapeSpmmDirectB8 ? 8 : 9;
         } else if ((shape == kShapeSpmmRing2 || shape == kShapeSpmmRing4) && batch >= 4) {
           op.spmm_buckets = false;
           op.spmm_variant = shape == kShapeSpmmRing2 ? 3 : 4;
@@ -598,7 +610,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_variant = 0;
           op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_variant == 7  ? kShapeSpmmBucketsB
+        op.shape = op.spmm_variant == 9  ? kShapeSpmmDirectB12
+                   : op.spmm_variant == 8  ? kShapeSpmmDirectB8
+                   : op.spmm_variant == 7  ? kShapeSpmmBucketsB
                    : op.spmm_variant == 6  ? kShapeSpmmDirectBLane
                    : op.spmm_variant == 5  ? kShapeSpmmDirectB
                    : op.spmm_variant == 3  ? kShapeSpmmRing2
@@ -674,16 +688,25 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
       ema_shape(op.cols_a, op.cols_p, elem, smem_cap, &op.ema_rows, &op.ema_rpl);
       const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
+      const bool sym = A.size - 1 == Pc.size && table_buf[C.a] == pbuf[C.p];
+      // default: vertex tiles when they fit (measured faster on R-MAT 20), else rows
+      op.ema_vrpl = ema_vertex_fits(batch, 1, op.ld_a, op.ld_p, sym, elem, smem_cap) ? 1 : 0;
       if ((shape == 64 || shape == 32 || shape == 16 || shape == 8 || shape == 4) &&
           (op.cols_a + op.cols_p) * elem * (shape + 1) <= smem_cap) {
         op.ema_rows = shape;
         op.ema_rpl = shape == 64 ? 2 : 1;
+        op.ema_vrpl = 0;
+      } else if ((shape == kShapeEmaVertex1 || shape == kShapeEmaVertex2) &&
+                 ema_vertex_fits(batch, shape - 100, op.ld_a, op.ld_p, sym, elem, smem_cap)) {
+        op.ema_vrpl = shape - 100;
       }
-      op.shape = op.ema_rows;
+      op.shape = op.ema_vrpl ? 100 + op.ema_vrpl : op.ema_rows;
       op.ema_sym = op.in_a == op.in_p && A.size - 1 == Pc.size;
       if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
+      // the vertex-tile kernel takes the raw split indices (rows 0, no column offset)
       op.tab_off = build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
-                                            &P->tabs, &tcache, op.ema_rows, op.cols_a)
+                                            &P->tabs, &tcache, op.ema_vrpl ? 0 : op.ema_rows,
+                                            op.ema_vrpl ? 0 : op.cols_a)
                               : 0;
       op.state_out = table_state[c] = n_states++;
       op.out = table_buf[c] = add_buf(P, "T" + std::to_string(c), rows * op.ld_out * elem, idx);
@@ -751,6 +774,11 @@ static bool tables_in_range(const Plan& P, int k) {
       if (n > left) return false;
       for (int64_t i = 0; i < n; ++i)
         if ((int)(t[i] & 0xffu) >= k || (int64_t)(t[i] >> 8) >= op.cols_p) return false;
+    } else if (op.kind == OP_EMA && op.ema_vrpl > 0) {
+      const int64_t n = 2 * op.cols_out * op.nsplit;
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; i += 2)
+        if (t[i] >= (uint32_t)op.cols_a || t[i + 1] >= (uint32_t)op.cols_p) return false;
     } else if (op.kind == OP_EMA) {
       const int64_t n = 2 * op.cols_out * op.nsplit;
       const uint32_t lim = (uint32_t)((op.cols_a + op.cols_p) * (op.ema_rows + 1));
@@ -774,6 +802,8 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
     c.push_back(kShapeSpmmDirect);
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
+    if (spmm_cols_per_lane(P.batch, op.cols_p) > 4) c.push_back(kShapeSpmmDirectB8);
+    if (spmm_cols_per_lane(P.batch, op.cols_p) > 8) c.push_back(kShapeSpmmDirectB12);
     if (spmm_cols_per_lane(P.batch, op.cols_p) <= 12) c.push_back(kShapeSpmmPrefetch);
     if (spmm_bucket_bytes(P.batch, P.k, op.cols_p, P.elem) <= kSpmmBucketTuneMaxBytes) {
       c.push_back(kShapeSpmmBuckets);
@@ -788,6 +818,8 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
   } else if (op.kind == OP_EMA) {
     for (int r : {64, 32, 16, 8})
       if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap) c.push_back(r);
+    for (int v : {1, 2})
+      if (ema_vertex_fits(P.batch, v, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap)) c.push_back(100 + v);
   }
   if (c.size() < 2) c.clear();
   return c;

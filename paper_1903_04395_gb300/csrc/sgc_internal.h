@@ -150,7 +150,8 @@ struct PlanOp {
   bool spmm_buckets = false; // SpMM: sum neighbour rows per neighbour color, resolve once per row
   int spmm_variant = 0;      // direct SpMM loop: 0 chunked, 1 next-neighbour prefetch, 3 / 4 ring
                              // of 2 / 4 asynchronous row copies, 5 / 6 compile-time batch with
-                             // the 32-bit / lane-major 16-bit position table;
+                             // the 32-bit / lane-major 16-bit position table, 8 / 9 compile-time
+                             // batch with 8 / 12 entries per lane in flight;
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -158,6 +159,8 @@ struct PlanOp {
   int shape = 0;             // launch shape code (kSpmm* / eMA rows), see op_shape_candidates
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_rpl = 1;           // eMA: rows per lane
+  int ema_vrpl = 0;          // eMA over vertex tiles (batch >= 4) with 1 or 2 rows per lane; 0 = rows
+                             // staged column-major (ema_rows)
   bool ema_sym = false;      // eMA of a table with itself (same buffer, |A| - 1 == |T_p|): each
                              // unordered split once, doubled
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
@@ -194,12 +197,15 @@ struct Plan {
 // The direct form can also stream neighbour rows through a ring of 2 or 4
 // shared-memory slots filled by asynchronous copies (batch >= 4), or run with
 // the batch as a compile-time constant (immediate offsets, shuffled ids) with
-// the 32-bit position table or a lane-major 16-bit one; likewise the
-// bucketed form (10).
+// the 32-bit position table or a lane-major 16-bit one, or with 8 / 12 entries
+// per lane in flight (11 / 12); likewise the bucketed form (10).
 constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3, kShapeSpmmRegBuckets = 4,
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
-              kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10;
+              kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
+              kShapeSpmmDirectB12 = 12;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
+// eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane)
+constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102;
 // entries per lane of the lane-major position table of the batch-specialised
 // direct form (L lanes per coloring; a multiple of 4 so a lane reads 4 at once)
 inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }

@@ -92,7 +92,7 @@ def test_recorded_sequence_replays_with_new_seeds(er_graph):
     assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
 
 
-@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_spmm_shape(precision, spmm_shape):
     sgc.build()
@@ -108,16 +108,19 @@ def test_every_spmm_shape(precision, spmm_shape):
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
-@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4])
-def test_every_ema_rows(ema_rows):
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 101, 102])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_ema_shape(ema_rows, precision):
     sgc.build()
     rp, ci = sgcgen.rmat(12, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=4)
     g = sgc.Graph(rp, ci)
-    for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8)):
+    # the spider's eMA is symmetric (a table with itself), the others are not;
+    # vertex tiles need 4..32 colorings per pass: 16 + 8 + 1 exercises both kernels
+    for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8), sgcgen.spider_tree([3, 3, 3])):
         t = sgc.Template(parent)
-        seeds = np.arange(20, 29, dtype=np.uint64)  # 8 + 1
-        r = sgc.count(g, t, seeds, precision="fp64", ema_rows=ema_rows)
-        check(r.maps, oracle_maps(rp, ci, parent, seeds), "fp64")
+        seeds = np.arange(20, 45, dtype=np.uint64)
+        r = sgc.count(g, t, seeds, precision=precision, ema_rows=ema_rows, batch=16)
+        check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
 def test_autotune_report_and_tuned_counts():
