@@ -684,13 +684,18 @@ def main():
         ops.append({"op": f"{e['name']}(t={e['t']},a={e['a']},p={e['p']})", "kind": e["name"],
                     "passes": e["passes"], "kernels": e["kernels"], "ms_per_pass": avg_ms,
                     "alg_bytes_per_pass": e["bytes"], "gbs": e["bytes"] / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0,
+                    "gather_bytes_per_pass": e["gather_bytes"],
+                    "gather_gbs": e["gather_bytes"] / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0,
                     "share": e["ms"] / max(sum(x["ms"] for x in prof), 1e-9)})
     ops.sort(key=lambda o: -o["share"])
     dom = ops[0]
     achieved = dom["gbs"]
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "traffic": recorded_traffic(dom["op"]), "kernel": dom["op"],
-                       "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'})"}
+                       "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'})",
+                       "gather_gbs": dom["gather_gbs"],
+                       "note": "achieved counts each table entry once (compulsory bytes); an SpMM gathers a "
+                               "neighbour's row once per stored entry: gather_gbs is that traffic (L2 + HBM) per second"}
     se = [o for o in ops if o["kind"] in ("spmm", "hist", "ema", "final", "final_leaf")]
     se_bytes = sum(o["alg_bytes_per_pass"] * o["passes"] for o in se)
     se_ms = sum(o["ms_per_pass"] * o["passes"] for o in se)

@@ -82,8 +82,9 @@ typedef struct sgc_options {
                           6 / 7 direct with neighbour rows streamed through a ring of 2 / 4
                           asynchronous copies (batch >= 4), 8 / 9 direct specialised for the
                           batch (9: with a lane-major 16-bit position table; 11 / 12: with 8 / 12
-                          entries per lane in flight), 10 bucketed specialised for the batch;
-                          ops it does not fit keep theirs.  0 (default) = planner or
+                          entries per lane in flight; 13: with a private accumulator column per
+                          lane), 10 bucketed specialised for the batch; ops it does not fit keep
+                          theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8 or 4 rows staged column-major per
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
@@ -229,8 +230,8 @@ typedef struct sgc_tune_entry {
   int32_t chosen;            /* index of the kept shape in shapes[] */
   int32_t shapes[8];         /* SpMM: 1 direct, 2 direct with prefetch, 3 bucketed, 4 register buckets,
                                 5 direct with packed positions, 6 / 7 direct with a copy ring,
-                                8 / 9 / 11 / 12 direct specialised for the batch, 10 bucketed
-                                specialised;
+                                8 / 9 / 11 / 12 / 13 direct specialised for the batch, 10
+                                bucketed specialised;
                                 eMA: rows staged per block, or 101 / 102 vertex tiles */
   double ms[8];              /* device time of the op, one pass, per shape */
 } sgc_tune_entry;
@@ -335,6 +336,8 @@ typedef struct sgc_op_profile {
   double bytes;      /* algorithmic bytes of one pass: every table read or written once,
                         CSR read once per column tile */
   double flops;      /* multiplies + adds of one pass (eMA and final step) */
+  double gather_bytes; /* SpMM and histogram: bytes of the neighbour rows gathered in one pass
+                          (every stored entry's row once, nnz * row bytes), served by L2 and HBM */
 } sgc_op_profile;
 
 /* Turn event recording around every op on (1) or off (0); turning it on

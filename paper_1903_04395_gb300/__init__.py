@@ -63,7 +63,8 @@ class sgc_server_stats(ctypes.Structure):
 class sgc_op_profile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("a", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("passes", ctypes.c_int64), ("kernels", ctypes.c_int64),
-                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double),
+                ("gather_bytes", ctypes.c_double)]
 
 
 class sgc_tune_entry(ctypes.Structure):
@@ -242,7 +243,8 @@ def sgc_count_many(g: int, templates, seeds, opt: sgc_options | None = None):
 
 SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buckets", 5: "direct+packed", 6: "direct+ring2",
                7: "direct+ring4", 8: "direct-batch",
-               9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12"}
+               9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12",
+               13: "direct-batch-private"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:

@@ -448,8 +448,8 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
   for (int32_t j = 0; j < n_t; ++j)
     if (o.root >= ts[j]->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmDirectB12)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..12");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmDirectBPriv)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..13");
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != kShapeEmaVertex1 && o.ema_rows != kShapeEmaVertex2)
     return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 101 or 102");
@@ -841,6 +841,7 @@ sgc_status sgc_profile_read(const sgc_graph* g, sgc_op_profile* out, int32_t cap
     out[i].ms = a.ms;
     out[i].bytes = a.bytes;
     out[i].flops = a.flops;
+    out[i].gather_bytes = a.gather;
   }
   g->prof.agg.clear();
   return SGC_OK;

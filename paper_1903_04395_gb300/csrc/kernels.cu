@@ -482,7 +482,13 @@ __global__ void __launch_bounds__(kBlock) k_spmm_direct_pf(
 // once (more loads in flight for wide rows); G = 0 takes four at a time.  Neighbour ids and their color words are read
 // 32 at a time, one per lane, and shuffled.  Same summation order as k_spmm's
 // direct form.
-template <typename T, int B, bool LM, int G>
+//
+// PRIV: every lane accumulates into its own shared-memory column
+// (acc[pos * 32 + lane], one bank per lane), so the scattered adds never
+// conflict; the L = 32 / B partial rows of a coloring are summed with warp
+// shuffles when the row is written (L * 32 * ld_out entries of shared memory
+// per warp instead of B * ld_out).
+template <typename T, int B, bool LM, int G, bool PRIV = false>
 __global__ void __launch_bounds__(kBlock) k_spmm_d(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
@@ -492,10 +498,12 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int L = 32 / B;
   constexpr int NW = B > 8 ? B / 8 : 1;  // color words per vertex
+  constexpr int AS = PRIV ? 32 : B;       // accumulator entries per position
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int acc_len = ld_out * B;
+  const int acc_len = ld_out * AS;
   T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const int ab = PRIV ? lane : lane % B;  // this lane's accumulator column
   const int b = lane % B, jl = lane / B;
   const int word = b >> 3, shift = (b & 7) * 8;
   const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
@@ -533,10 +541,10 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
             const T x1 = q + 1 < ns ? __ldg(src + 32 * (q + 1)) : T(0);
             const T x2 = q + 2 < ns ? __ldg(src + 32 * (q + 2)) : T(0);
             const T x3 = q + 3 < ns ? __ldg(src + 32 * (q + 3)) : T(0);
-            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
-            if (p1 < (uint32_t)ld_out) acc[p1 * B + b] += x1;
-            if (p2 < (uint32_t)ld_out) acc[p2 * B + b] += x2;
-            if (p3 < (uint32_t)ld_out) acc[p3 * B + b] += x3;
+            if (p0 < (uint32_t)ld_out) acc[p0 * AS + ab] += x0;
+            if (p1 < (uint32_t)ld_out) acc[p1 * AS + ab] += x1;
+            if (p2 < (uint32_t)ld_out) acc[p2 * AS + ab] += x2;
+            if (p3 < (uint32_t)ld_out) acc[p3 * AS + ab] += x3;
           }
         } else if (G == 0) {  // 32-bit table [c_v][c_u][j], four entries at a time
           const uint32_t* pt = tab + (cvk + cu) * w_in + jl;
@@ -545,15 +553,15 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
             const uint32_t p0 = pt[L * q], p1 = pt[L * (q + 1)], p2 = pt[L * (q + 2)], p3 = pt[L * (q + 3)];
             const T x0 = __ldg(src + 32 * q), x1 = __ldg(src + 32 * (q + 1));
             const T x2 = __ldg(src + 32 * (q + 2)), x3 = __ldg(src + 32 * (q + 3));
-            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
-            if (p1 < (uint32_t)ld_out) acc[p1 * B + b] += x1;
-            if (p2 < (uint32_t)ld_out) acc[p2 * B + b] += x2;
-            if (p3 < (uint32_t)ld_out) acc[p3 * B + b] += x3;
+            if (p0 < (uint32_t)ld_out) acc[p0 * AS + ab] += x0;
+            if (p1 < (uint32_t)ld_out) acc[p1 * AS + ab] += x1;
+            if (p2 < (uint32_t)ld_out) acc[p2 * AS + ab] += x2;
+            if (p3 < (uint32_t)ld_out) acc[p3 * AS + ab] += x3;
           }
           for (; q < ns; ++q) {
             const uint32_t p0 = pt[L * q];
             const T x0 = __ldg(src + 32 * q);
-            if (p0 < (uint32_t)ld_out) acc[p0 * B + b] += x0;
+            if (p0 < (uint32_t)ld_out) acc[p0 * AS + ab] += x0;
           }
         } else {  // 32-bit table, G entries per lane in flight at once (predicated)
           constexpr int GG = G > 0 ? G : 1;
@@ -569,17 +577,38 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
             }
 #pragma unroll
             for (int i = 0; i < GG; ++i)
-              if (pp[i] < (uint32_t)ld_out) acc[pp[i] * B + b] += xx[i];
+              if (pp[i] < (uint32_t)ld_out) acc[pp[i] * AS + ab] += xx[i];
           }
         }
         __syncwarp();
       }
     }
-    T* dst = it.heavy ? scratch + item * (int64_t)acc_len : P + (int64_t)it.row * acc_len;
-    for (int i = lane; i < acc_len; i += 32) {
-      const T x = acc[i];
-      dst[i] = x;
-      if (!it.heavy) m = fmaxf(m, (float)x);
+    const int out_len = ld_out * B;
+    T* dst = it.heavy ? scratch + item * (int64_t)out_len : P + (int64_t)it.row * out_len;
+    if (PRIV) {
+      // positions g*L .. g*L+L-1: lane (jl, b) ends up holding position g*L + jl of coloring b
+      // summed over the L partial columns, and writes dst[g * 32 + lane] (coalesced)
+      __syncwarp();
+      for (int g = 0; g * L < ld_out; ++g) {
+        T mine = T(0);
+#pragma unroll
+        for (int r = 0; r < L; ++r) {
+          T v = g * L + r < ld_out ? acc[(g * L + r) * 32 + lane] : T(0);
+#pragma unroll
+          for (int o = B; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (r == jl) mine = v;
+        }
+        if (g * L + jl < ld_out) {
+          dst[g * 32 + lane] = mine;
+          if (!it.heavy) m = fmaxf(m, (float)mine);
+        }
+      }
+    } else {
+      for (int i = lane; i < acc_len; i += 32) {
+        const T x = acc[i];
+        dst[i] = x;
+        if (!it.heavy) m = fmaxf(m, (float)x);
+      }
     }
     __syncwarp();
   }
@@ -1334,7 +1363,7 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
   } while (0)
-    if (variant == 5 || variant == 6 || variant == 8 || variant == 9) {
+    if (variant == 5 || variant == 6 || variant == 8 || variant == 9 || variant == 10) {
 #define SGC_D(B_, LM_, G_)                                                                                   \
   do {                                                                                                       \
     allow_smem(k_spmm_d<T, B_, LM_, G_>, smem);                                                              \
@@ -1342,9 +1371,18 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
         colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, nsp, si, so);         \
   } while (0)
+#define SGC_DP(B_)                                                                                           \
+  do {                                                                                                       \
+    allow_smem(k_spmm_d<T, B_, false, 0, true>, smem_priv);                                                  \
+    k_spmm_d<T, B_, false, 0, true><<<grid_for(nitems, wpb_priv, 1 << 30), 32 * wpb_priv, smem_priv, st>>>( \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
+        colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, nsp, si, so);         \
+  } while (0)
 #define SGC_D2(B_)                   \
   do {                               \
-    if (variant == 6)                \
+    if (variant == 10)               \
+      SGC_DP(B_);                    \
+    else if (variant == 6)           \
       SGC_D(B_, true, 0);            \
     else if (variant == 8)           \
       SGC_D(B_, false, 8);           \
@@ -1354,6 +1392,13 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
       SGC_D(B_, false, 0);           \
   } while (0)
       const int nsp = (int)spmm_lane_nsp(op.cols_p, 32 / batch);
+      // private accumulator columns: 32 entries per output position per warp
+      const size_t per_warp_priv = (size_t)op.ld_out * 32 * sizeof(T);
+      int wpb_priv = kBlock / 32;
+      while (wpb_priv > 1 && per_warp_priv * wpb_priv > smem_cap) wpb_priv /= 2;
+      const size_t smem_priv = per_warp_priv * wpb_priv;
+      if (variant == 10 && smem_priv > smem_cap)
+        return fail(SGC_ERR_UNSUPPORTED, "SpMM private accumulators do not fit in shared memory");
       switch (batch) {
         case 1: SGC_D2(1); break;
         case 2: SGC_D2(2); break;
@@ -1363,6 +1408,7 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         default: SGC_D2(32); break;
       }
 #undef SGC_D2
+#undef SGC_DP
 #undef SGC_D
     } else if (variant >= 3 && batch >= 4) {
       // asynchronous-copy ring of R = 2 (variant 3) or 4 (variant 4) neighbour rows per warp
@@ -1483,6 +1529,7 @@ int profile_slot(Profiler* prof, const PlanOp& op, int batch) {
   a.batch = batch;
   a.bytes = op.alg_bytes;
   a.flops = op.alg_flops;
+  a.gather = op.gather_bytes;
   prof->agg.push_back(a);
   return (int)prof->agg.size() - 1;
 }

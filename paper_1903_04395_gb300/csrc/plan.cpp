@@ -564,6 +564,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.kind = OP_HIST;
         op.in_p = P->buf_colors;
         op.alg_bytes = 4 * (nv + 1) + 4 * nnz + nv * batch + (double)elem * nv * batch * (double)op.cols_out;
+        op.gather_bytes = nnz * (double)batch;  // one color byte per stored entry and coloring
         double by = nnz * 4 + nnz * 1 + nv * (double)op.cols_out * elem;
         P->est_bytes += by;
         P->est_spmm_bytes += by;
@@ -599,6 +600,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         } else if (shape == kShapeSpmmDirectBLane && op.ld_out < 65535) {
           op.spmm_buckets = false;
           op.spmm_variant = 6;
+        } else if (shape == kShapeSpmmDirectBPriv && op.ld_out * 32 * elem <= kSpmmPrivMaxBytes) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 10;
         } else if (shape == kShapeSpmmDirectB8 || shape == kShapeSpmmDirectB12) {
           op.spmm_buckets = false;
           op.spmm_variant = shape == kShapeSpmmDirectB8 ? 8 : 9;
@@ -610,7 +614,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_variant = 0;
           op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_variant == 9  ? kShapeSpmmDirectB12
+        op.shape = op.spmm_variant == 10 ? kShapeSpmmDirectBPriv
+                   : op.spmm_variant == 9  ? kShapeSpmmDirectB12
                    : op.spmm_variant == 8  ? kShapeSpmmDirectB8
                    : op.spmm_variant == 7  ? kShapeSpmmBucketsB
                    : op.spmm_variant == 6  ? kShapeSpmmDirectBLane
@@ -631,6 +636,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                                            : build_table(cr, k, OP_SPMM, Pc.size, 0, &P->tabs, &tcache);
         max_spmm_width = std::max<int64_t>(max_spmm_width, op.ld_out * batch);
         op.alg_bytes = 4 * (nv + 1 + nnz) + nv * batch + (double)elem * nv * batch * (double)(op.cols_p + op.cols_out);
+        op.gather_bytes = nnz * (double)batch * (double)op.cols_p * elem;
         double by = nnz * 4 + (double)elem * nv * (double)(op.cols_p + op.cols_out);
         P->est_bytes += by;
         P->est_spmm_bytes += by;
@@ -804,6 +810,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
     if (spmm_cols_per_lane(P.batch, op.cols_p) > 4) c.push_back(kShapeSpmmDirectB8);
     if (spmm_cols_per_lane(P.batch, op.cols_p) > 8) c.push_back(kShapeSpmmDirectB12);
+    if (op.ld_out * 32 * P.elem <= kSpmmPrivMaxBytes) c.push_back(kShapeSpmmDirectBPriv);
     if (spmm_cols_per_lane(P.batch, op.cols_p) <= 12) c.push_back(kShapeSpmmPrefetch);
     if (spmm_bucket_bytes(P.batch, P.k, op.cols_p, P.elem) <= kSpmmBucketTuneMaxBytes) {
       c.push_back(kShapeSpmmBuckets);

@@ -51,6 +51,7 @@ struct OpProfile {
   int64_t launches = 0;   // passes recorded
   int64_t kernels = 0;    // kernel launches of those passes
   double ms = 0, bytes = 0, flops = 0;  // summed time; algorithmic bytes / flops per pass
+  double gather = 0;                    // SpMM: gathered neighbour-row bytes per pass
 };
 
 struct PendingEvent {
@@ -151,7 +152,8 @@ struct PlanOp {
   int spmm_variant = 0;      // direct SpMM loop: 0 chunked, 1 next-neighbour prefetch, 3 / 4 ring
                              // of 2 / 4 asynchronous row copies, 5 / 6 compile-time batch with
                              // the 32-bit / lane-major 16-bit position table, 8 / 9 compile-time
-                             // batch with 8 / 12 entries per lane in flight;
+                             // batch with 8 / 12 entries per lane in flight, 10 private
+                             // accumulator columns;
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -167,6 +169,7 @@ struct PlanOp {
   int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
   double alg_bytes = 0;      // algorithmic HBM bytes of one pass (tables read / written once)
   double alg_flops = 0;      // multiply + add count of one pass
+  double gather_bytes = 0;   // SpMM / histogram: neighbour-row bytes gathered in one pass
 };
 
 struct Plan {
@@ -198,11 +201,14 @@ struct Plan {
 // shared-memory slots filled by asynchronous copies (batch >= 4), or run with
 // the batch as a compile-time constant (immediate offsets, shuffled ids) with
 // the 32-bit position table or a lane-major 16-bit one, or with 8 / 12 entries
-// per lane in flight (11 / 12); likewise the bucketed form (10).
+// per lane in flight (11 / 12), or with one private accumulator column per
+// lane (13, conflict-free adds); likewise the bucketed form (10).
 constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3, kShapeSpmmRegBuckets = 4,
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
-              kShapeSpmmDirectB12 = 12;
+              kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13;
+// private accumulator columns (shape 13) are tried while a warp's fit in this
+constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
 // eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane)
 constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102;

@@ -92,7 +92,7 @@ def test_recorded_sequence_replays_with_new_seeds(er_graph):
     assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
 
 
-@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_spmm_shape(precision, spmm_shape):
     sgc.build()
