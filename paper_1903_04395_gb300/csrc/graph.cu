@@ -33,35 +33,89 @@ __global__ void k_check_rowptr(const int32_t* __restrict__ rp, int32_t n, int64_
   }
 }
 
-// one warp per row: range, self-loop, strictly ascending, and symmetry by
-// binary search of v in row u (rows are sorted once the previous checks pass)
-__global__ void k_check_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
-                             int32_t* flags) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+// One warp per row: range, self-loop, strictly ascending, and symmetry.
+// Symmetry is checked from one side of each entry only: with key(x) =
+// (deg x, x), an entry (v, u) with key(u) < key(v) is "searched" (v must be
+// found, by binary search, in the shorter row u); otherwise it is "skipped".
+// If every searched entry is found, mirroring maps searched entries one-to-one
+// onto skipped ones (rows have no duplicates), so the adjacency is symmetric
+// exactly when, in addition, both kinds are equally many (counts[0] ==
+// counts[1], compared on the host).  The searches run in the shorter row of
+// each pair, so hub rows are never searched from their many light neighbours.
+//
+// Rows longer than kWideRow are left to k_check_cols_wide (a block per row),
+// so no warp walks a hub's whole neighbour list alone.
+constexpr int32_t kWideRow = 2048;
+
+__device__ __forceinline__ int32_t check_entry(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                               int32_t n, int64_t v, int32_t lo, int32_t dv, int32_t e,
+                                               unsigned long long* searched, unsigned long long* skipped) {
+  const int32_t u = ci[e];
+  if (u < 0 || u >= n) return BAD_COL;
+  int32_t f = 0;
+  if (u == v) f |= SELF_LOOP;
+  if (e > lo && ci[e - 1] >= u) f |= UNSORTED;
+  int32_t a = rp[u], b = rp[u + 1] - 1;
+  const int32_t du = b + 1 - a;
+  if (du > dv || (du == dv && u >= v)) {
+    ++*skipped;
+    return f;
+  }
+  ++*searched;
+  bool found = false;
+  int guard = 0;
+  while (a <= b && guard < 40) {
+    const int32_t mid = a + ((b - a) >> 1);
+    const int32_t x = ci[mid];
+    if (x == v) { found = true; break; }
+    if (x < v) a = mid + 1; else b = mid - 1;
+    ++guard;
+  }
+  return found ? f : (f | ASYMMETRIC);
+}
+
+__device__ __forceinline__ void add_counts(unsigned long long* counts, unsigned long long searched,
+                                           unsigned long long skipped) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    searched += __shfl_xor_sync(0xffffffffu, searched, o);
+    skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (searched | skipped)) {
+    atomicAdd(counts, searched);
+    atomicAdd(counts + 1, skipped);
+  }
+}
+
+__global__ void k_check_cols_wide(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                  const int32_t* __restrict__ wide, int32_t n_wide, int32_t* flags,
+                                  unsigned long long* counts) {
+  unsigned long long searched = 0, skipped = 0;
+  for (int32_t w = blockIdx.x; w < n_wide; w += gridDim.x) {
+    const int64_t v = wide[w];
     const int32_t lo = rp[v], hi = rp[v + 1];
     int32_t f = 0;
-    for (int32_t e = lo + lane; e < hi; e += 32) {
-      const int32_t u = ci[e];
-      if (u < 0 || u >= n) { f |= BAD_COL; continue; }
-      if (u == v) f |= SELF_LOOP;
-      if (e > lo && ci[e - 1] >= u) f |= UNSORTED;
-      // symmetric: v must appear in row u
-      int32_t a = rp[u], b = rp[u + 1] - 1;
-      bool found = false;
-      int guard = 0;
-      while (a <= b && guard < 40) {
-        const int32_t mid = a + ((b - a) >> 1);
-        const int32_t x = ci[mid];
-        if (x == v) { found = true; break; }
-        if (x < v) a = mid + 1; else b = mid - 1;
-        ++guard;
-      }
-      if (!found) f |= ASYMMETRIC;
-    }
+    for (int32_t e = lo + threadIdx.x; e < hi; e += blockDim.x)
+      f |= check_entry(rp, ci, n, v, lo, hi - lo, e, &searched, &skipped);
     if (f) atomicOr(flags, f);
   }
+  add_counts(counts, searched, skipped);
+}
+
+__global__ void k_check_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                             int32_t* flags, unsigned long long* counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long searched = 0, skipped = 0;
+  for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+    const int32_t lo = rp[v], hi = rp[v + 1];
+    const int32_t dv = hi - lo;
+    if (dv > kWideRow) continue;
+    int32_t f = 0;
+    for (int32_t e = lo + lane; e < hi; e += 32) f |= check_entry(rp, ci, n, v, lo, dv, e, &searched, &skipped);
+    if (f) atomicOr(flags, f);
+  }
+  add_counts(counts, searched, skipped);  // one pair of atomics per warp
 }
 
 // new row v copies old row orig[v] with neighbours renamed through inv.
@@ -69,26 +123,41 @@ __global__ void k_check_cols(const int32_t* __restrict__ rp, const int32_t* __re
 // malformed CSR is reported instead of read out of bounds later; an entry
 // pointing at an isolated vertex (possible only without symmetry) is
 // reported the same way.
+//
+// The first n_wide new rows (the longest, degree order) get a block each; the
+// rest a warp each.
+__device__ __forceinline__ void relabel_entry(const int32_t* __restrict__ old_ci, int32_t n,
+                                              const int32_t* __restrict__ inv, int64_t src, int64_t dst,
+                                              int32_t* __restrict__ new_ci, int32_t* flags) {
+  const int32_t u = old_ci[src];
+  int32_t w = 0;
+  if (u < 0 || u >= n) {
+    atomicOr(flags, BAD_COL);
+  } else {
+    w = inv[u];
+    if (w < 0) { atomicOr(flags, ASYMMETRIC); w = 0; }
+  }
+  new_ci[dst] = w;
+}
+
 __global__ void k_relabel(const int32_t* __restrict__ old_rp, const int32_t* __restrict__ old_ci, int32_t n,
                           const int32_t* __restrict__ orig, const int32_t* __restrict__ inv,
-                          const int32_t* __restrict__ new_rp, int32_t n_act, int32_t* __restrict__ new_ci,
-                          int32_t* flags) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_act; v += nw) {
+                          const int32_t* __restrict__ new_rp, int32_t n_act, int32_t n_wide,
+                          int32_t* __restrict__ new_ci, int32_t* flags) {
+  if ((int32_t)blockIdx.x < n_wide) {  // one long row per block
+    const int32_t v = blockIdx.x;
     const int32_t o = orig[v];
     const int32_t lo = old_rp[o], deg = old_rp[o + 1] - lo, dst = new_rp[v];
-    for (int32_t j = lane; j < deg; j += 32) {
-      const int32_t u = old_ci[lo + j];
-      int32_t w = 0;
-      if (u < 0 || u >= n) {
-        atomicOr(flags, BAD_COL);
-      } else {
-        w = inv[u];
-        if (w < 0) { atomicOr(flags, ASYMMETRIC); w = 0; }
-      }
-      new_ci[dst + j] = w;
-    }
+    for (int32_t j = threadIdx.x; j < deg; j += blockDim.x) relabel_entry(old_ci, n, inv, lo + j, dst + j, new_ci, flags);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)(gridDim.x - n_wide) * (blockDim.x >> 5);
+  for (int64_t v = n_wide + (blockIdx.x - n_wide) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_act;
+       v += nw) {
+    const int32_t o = orig[v];
+    const int32_t lo = old_rp[o], deg = old_rp[o + 1] - lo, dst = new_rp[v];
+    for (int32_t j = lane; j < deg; j += 32) relabel_entry(old_ci, n, inv, lo + j, dst + j, new_ci, flags);
   }
 }
 
@@ -158,19 +227,38 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
     if (h_rp[v + 1] < h_rp[v]) return fail(SGC_ERR_INVALID, "row_ptr must be non-decreasing");
   if (flags & SGC_GRAPH_VALIDATE) {
     if (nnz % 2 != 0) return fail(SGC_ERR_INVALID, "an undirected simple graph has an even nnz");
+    // flags word, then the searched / skipped entry counts of the symmetry check
     int32_t* d_flags = nullptr;
-    SGC_CUDA_TRY(cudaMalloc(&d_flags, sizeof(int32_t)));
+    SGC_CUDA_TRY(cudaMalloc(&d_flags, 3 * sizeof(unsigned long long)));
+    unsigned long long* d_counts = reinterpret_cast<unsigned long long*>(d_flags) + 1;
     int32_t h_flags = 0;
-    cudaError_t e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
+    unsigned long long h_counts[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d_flags, 0, 3 * sizeof(unsigned long long), st);
+    // rows longer than kWideRow, checked a block per row
+    std::vector<int32_t> wide;
+    for (int32_t v = 0; v < n; ++v)
+      if (h_rp[v + 1] - h_rp[v] > kWideRow) wide.push_back(v);
+    int32_t* d_wide = nullptr;
+    if (e == cudaSuccess && !wide.empty()) {
+      e = cudaMalloc(&d_wide, wide.size() * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_wide, wide.data(), wide.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess && n > 0) {
       k_check_rowptr<<<std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(d_rp, n, nnz, d_flags);
-      k_check_cols<<<std::min<int64_t>((n + 7) / 8, 65536), 256, 0, st>>>(d_rp, d_ci, n, d_flags);
+      k_check_cols<<<std::min<int64_t>((n + 7) / 8, 65536), 256, 0, st>>>(d_rp, d_ci, n, d_flags, d_counts);
+      if (!wide.empty())
+        k_check_cols_wide<<<std::min<int64_t>((int64_t)wide.size(), 65536), 256, 0, st>>>(
+            d_rp, d_ci, n, d_wide, (int32_t)wide.size(), d_flags, d_counts);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_counts, sizeof(h_counts), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_flags);
+    if (d_wide) cudaFree(d_wide);
     if (e != cudaSuccess) return cuda_fail(e, "graph validation");
+    if (!(h_flags & (BAD_ROWPTR | BAD_COL)) && h_counts[0] != h_counts[1]) h_flags |= ASYMMETRIC;
     if (h_flags) {
       std::string why;
       if (h_flags & BAD_ROWPTR) why += " row_ptr out of range;";
@@ -234,8 +322,11 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
   if (e == cudaSuccess) e = cudaMalloc(&d_flags, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
   if (e == cudaSuccess && n_act > 0) {
-    k_relabel<<<std::min<int64_t>((n_act + 7) / 8, 65536), 256, 0, st>>>(d_rp, d_ci, n, g->d_orig, d_inv,
-                                                                        g->d_row_ptr, n_act, g->d_col_idx, d_flags);
+    int32_t n_wide = 0;  // rows in degree order: the long ones are a prefix
+    while (n_wide < n_act && n_wide < 65536 && g->h_degree_sorted[(size_t)n_wide] > kWideRow) ++n_wide;
+    const int64_t light_blocks = std::min<int64_t>((n_act - n_wide + 7) / 8, 65536);
+    k_relabel<<<n_wide + std::max<int64_t>(light_blocks, 1), 256, 0, st>>>(
+        d_rp, d_ci, n, g->d_orig, d_inv, g->d_row_ptr, n_act, n_wide, g->d_col_idx, d_flags);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);

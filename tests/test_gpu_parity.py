@@ -201,6 +201,9 @@ _BAD_CSR = {
     "col_range": (_GOOD_RP, [1, 0, 2, 1, 3, 4]),
     "row_ptr": ([0, 3, 1, 5, 6], _GOOD_CI),
     "nnz_mismatch": ([0, 1, 3, 5, 7], _GOOD_CI + [0]),
+    # star 0-{1,2,3} plus directed entries 4->0 and 5->0: every mirror search succeeds, the
+    # one-sided entries are only caught by the searched / skipped entry counts
+    "asymmetric_one_sided": ([0, 3, 4, 5, 6, 7, 8], [1, 2, 3, 0, 0, 0, 0, 0]),
 }
 
 
