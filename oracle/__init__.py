@@ -53,13 +53,17 @@ def _load():
             lib.oracle_count.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32,
                                          P(ctypes.c_int32), P(ctypes.c_uint8), ctypes.c_int32, ctypes.c_int32,
                                          P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
+            lib.oracle_count_colors.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                                ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32),
+                                                P(ctypes.c_uint8), ctypes.c_int32, ctypes.c_int32,
+                                                P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
             lib.oracle_automorphisms.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_uint64)]
             lib.oracle_colorset_index.argtypes = [P(ctypes.c_int32), ctypes.c_int32]
             lib.oracle_colorset_index.restype = ctypes.c_int64
             lib.oracle_colorset_unindex.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                     P(ctypes.c_int32)]
-            for f in (lib.oracle_color, lib.oracle_count, lib.oracle_automorphisms, lib.oracle_colorset_unindex,
-                      lib.oracle_threads):
+            for f in (lib.oracle_color, lib.oracle_count, lib.oracle_count_colors, lib.oracle_automorphisms,
+                      lib.oracle_colorset_unindex, lib.oracle_threads):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -113,8 +117,9 @@ class CountResult:
 
 
 def count(row_ptr, col_idx, parent, cols, mode: str = "pruned", root: int | None = None,
-          per_vertex: bool = False) -> CountResult:
-    """Exact colorful maps of tree ``parent`` in graph (row_ptr, col_idx) under coloring ``cols``."""
+          per_vertex: bool = False, ncolors: int | None = None) -> CountResult:
+    """Exact colorful maps of tree ``parent`` in graph (row_ptr, col_idx) under coloring ``cols``
+    (colors in [0, ncolors), ncolors >= |T|, default |T|: Section 2.1 allows k >= |T| colors)."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
     ci, cip = _i32(col_idx if len(col_idx) else np.zeros(1, np.int32))
@@ -126,8 +131,8 @@ def count(row_ptr, col_idx, parent, cols, mode: str = "pruned", root: int | None
     mx = (ctypes.c_uint64 * 2)()
     pv = np.zeros((max(n, 1), 2), dtype=np.uint64) if per_vertex else None
     pvp = pv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if per_vertex else None
-    rc = lib.oracle_count(n, rpp, cip, len(par), parp, colp, {"pruned": 0, "literal": 1}[mode],
-                          -1 if root is None else int(root), maps, mx, pvp)
+    rc = lib.oracle_count_colors(n, rpp, cip, len(par), len(par) if ncolors is None else int(ncolors), parp, colp,
+                                 {"pruned": 0, "literal": 1}[mode], -1 if root is None else int(root), maps, mx, pvp)
     _check(rc)
     res = CountResult(maps=int(maps[0]) | (int(maps[1]) << 64), max_intermediate=int(mx[0]) | (int(mx[1]) << 64))
     if per_vertex:
@@ -154,16 +159,23 @@ class Estimate:
     max_intermediate: int
 
 
-def estimate(row_ptr, col_idx, parent, seeds, mode: str = "pruned") -> Estimate:
-    """Per-coloring colorful counts and the color-coding estimate k^k/k! * copies, averaged."""
-    k = len(parent)
+def colorful_probability(t: int, k: int) -> Fraction:
+    """Probability that t vertices get t distinct colors out of k uniform ones: k! / ((k - t)! k^t)."""
+    return Fraction(math.factorial(k), math.factorial(k - t) * k ** t)
+
+
+def estimate(row_ptr, col_idx, parent, seeds, mode: str = "pruned", ncolors: int | None = None) -> Estimate:
+    """Per-coloring colorful counts and the color-coding estimate copies / P(colorful), averaged
+    (k^k / k! * copies for k = |T| colors, Section 2.1)."""
+    t = len(parent)
+    k = t if ncolors is None else int(ncolors)
     n = len(row_ptr) - 1
     aut = automorphisms(parent)
-    scale = Fraction(k ** k, math.factorial(k))
+    scale = 1 / colorful_probability(t, k)
     maps, copies, ests = [], [], []
     mx = 0
     for s in seeds:
-        r = count(row_ptr, col_idx, parent, colors(int(s), n, k), mode=mode)
+        r = count(row_ptr, col_idx, parent, colors(int(s), n, k), mode=mode, ncolors=k)
         if r.maps % aut != 0:
             raise ArithmeticError("oracle: maps not divisible by |Aut(T)|")
         maps.append(r.maps)

@@ -34,7 +34,10 @@
  *   4. maps = sum_v N(v, T, {0..k-1}): the number of colorful injective
  *      edge-preserving maps T -> G.  copies = maps / |Aut(T)|, and the
  *      estimate of the number of (non-induced) copies is
- *      copies * k^k / k! (Section 2.1, item 1).
+ *      copies * k^k / k! (Section 2.1, item 1).  With k > |T| colors
+ *      (Section 2.1 allows k >= |T|) the maps sum the root table over every
+ *      |T|-subset of colors, and the estimate scales by the inverse of the
+ *      probability k! / ((k - |T|)! k^|T|) that a fixed copy is colorful.
  *
  * All counts are exact unsigned 128-bit integers; every add and multiply is
  * overflow-checked and an overflow makes the call return ORACLE_OVERFLOW.
@@ -339,36 +342,44 @@ static void put_u128(u128 x, uint64_t* out) {
 }
 
 /*
- * Colorful maps of the tree `parent` (k vertices, parent[root] = -1) into the
- * graph (CSR, n vertices) under `colors` (values in [0,k)).
+ * Colorful maps of the tree `parent` (t vertices, parent[root] = -1) into the
+ * graph (CSR, n vertices) under `colors` (values in [0, ncolors), ncolors >= t:
+ * Section 2.1 draws colors from k >= |T|).  A map is colorful when its t
+ * images have t distinct colors; the DP runs over color sets of the ncolors
+ * colors and the result sums the root table over every t-subset:
+ *   maps = sum_v sum_{C, |C| = t} N(v, T, C).
  *   mode: 0 = pruned (neighbour sums hoisted, Eq. 2), 1 = literal (Algorithm 1 order)
  *   root: template vertex used as the DP root, or -1 for parent's root
- *   maps_out[2]: low/high 64 bits of maps = sum_v N(v, T, all colors)
+ *   maps_out[2]: low/high 64 bits of maps
  *   max_out[2]:  largest value held in any table, buffer or the final sum
- *   per_vertex:  NULL, or n x 2 uint64 receiving N(v, T, all colors)
+ *   per_vertex:  NULL, or n x 2 uint64 receiving sum_C N(v, T, C)
  * Returns ORACLE_OK, ORACLE_OVERFLOW, ORACLE_EINVAL or ORACLE_ENOMEM.
  */
-int oracle_count(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k,
-                 const int32_t* parent, const uint8_t* colors, int32_t mode, int32_t root,
-                 uint64_t* maps_out, uint64_t* max_out, uint64_t* per_vertex) {
-  if (n < 0 || k < 1 || k > ORACLE_MAXK || (mode != 0 && mode != 1)) return ORACLE_EINVAL;
-  for (int32_t v = 0; v < n; ++v) if (colors[v] >= k) return ORACLE_EINVAL;
+int oracle_count_colors(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t t, int32_t ncolors,
+                        const int32_t* parent, const uint8_t* colors, int32_t mode, int32_t root,
+                        uint64_t* maps_out, uint64_t* max_out, uint64_t* per_vertex) {
+  if (n < 0 || t < 1 || t > ORACLE_MAXK || ncolors < t || ncolors > ORACLE_MAXK || (mode != 0 && mode != 1))
+    return ORACLE_EINVAL;
+  for (int32_t v = 0; v < n; ++v) if (colors[v] >= ncolors) return ORACLE_EINVAL;
   init_binom();
   dp_ctx ctx;
   memset(&ctx, 0, sizeof(ctx));
-  ctx.n = n; ctx.k = k; ctx.row_ptr = row_ptr; ctx.col_idx = col_idx;
+  ctx.n = n; ctx.k = ncolors; ctx.row_ptr = row_ptr; ctx.col_idx = col_idx;
   ctx.colors = colors; ctx.mode = mode;
-  int32_t r = root_template(&ctx, k, parent, root);
+  int32_t r = root_template(&ctx, t, parent, root);
   if (r < 0) return ORACLE_EINVAL;
   table full;
   int rc = subtemplate_table(&ctx, r, 0, &full);
   if (rc != ORACLE_OK) return rc;
-  /* full.ncols == binom(k,k) == 1 */
+  /* full.ncols == binom(ncolors, t): 1 when ncolors == t */
   u128 maps = 0;
   int ovf = 0;
   for (int32_t v = 0; v < n; ++v) {
-    ovf |= __builtin_add_overflow(maps, full.m[v], &maps);
-    if (per_vertex) put_u128(full.m[v], per_vertex + 2 * (int64_t)v);
+    u128 row = 0;
+    for (int64_t i = 0; i < full.ncols; ++i) ovf |= __builtin_add_overflow(row, full.m[(int64_t)v * full.ncols + i], &row);
+    ovf |= __builtin_add_overflow(maps, row, &maps);
+    if (row > ctx.max_seen) ctx.max_seen = row;
+    if (per_vertex) put_u128(row, per_vertex + 2 * (int64_t)v);
   }
   free(full.m);
   if (ovf) return ORACLE_OVERFLOW;
@@ -383,6 +394,13 @@ int oracle_count(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int3
  * itself is an automorphism, and with the identity coloring c(i) = i every
  * such map is colorful, so |Aut(T)| is the DP's maps count of T in T.
  */
+/* k colors for a k-vertex tree (Section 2.1 with k = |T|) */
+int oracle_count(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k, const int32_t* parent,
+                 const uint8_t* colors, int32_t mode, int32_t root, uint64_t* maps_out, uint64_t* max_out,
+                 uint64_t* per_vertex) {
+  return oracle_count_colors(n, row_ptr, col_idx, k, k, parent, colors, mode, root, maps_out, max_out, per_vertex);
+}
+
 int oracle_automorphisms(int32_t k, const int32_t* parent, uint64_t* aut_out) {
   if (k < 1 || k > ORACLE_MAXK) return ORACLE_EINVAL;
   int32_t deg[ORACLE_MAXK + 1];

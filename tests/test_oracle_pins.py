@@ -214,3 +214,56 @@ def test_invalid_templates_rejected():
         oracle.count(rp, ci, np.array([1, 2, 0], np.int32), cols)     # cycle, no root
     with pytest.raises(ValueError):
         oracle.count(rp, ci, np.array([-1, 0], np.int32), np.full(10, 3, np.uint8))  # color >= k
+
+
+# ---------------------------------------------------------------- k > |T| colors
+# Section 2.1 draws colors from k >= |T|; a map is colorful when its |T| images
+# get |T| distinct colors, and the estimate divides by k! / ((k - |T|)! k^|T|).
+
+@pytest.mark.parametrize("name,graph", list(_small_graphs()))
+def test_more_colors_brute_force(name, graph):
+    rp, ci = graph
+    n = len(rp) - 1
+    for parent in SMALL_TREES:
+        t = len(parent)
+        if t > 5:
+            continue
+        for extra in (1, 2):
+            k = t + extra
+            for seed in (1, 2):
+                cols = oracle.colors(seed, n, k)
+                want = pins.brute_force_maps(rp, ci, parent, cols)
+                assert oracle.count(rp, ci, parent, cols, ncolors=k).maps == want, (name, list(parent), k, seed)
+                assert oracle.count(rp, ci, parent, cols, ncolors=k, mode="literal").maps == want
+
+
+def test_more_colors_complete_graph():
+    # K_n: every injective map is edge-preserving, so the colorful maps of a t-tree are the ordered
+    # t-tuples of vertices with distinct colors: t! * e_t(n_0, ..., n_{k-1}) (elementary symmetric)
+    n = 30
+    rp, ci = sgcgen.complete_graph(n)
+    for parent, k in ((sgcgen.path_tree(4), 6), (sgcgen.pruefer_tree(5, 2), 7), (sgcgen.star_tree(3), 9)):
+        t = len(parent)
+        for seed in (3, 4):
+            counts = np.bincount(oracle.colors(seed, n, k), minlength=k)
+            e_t = sum(math.prod(int(counts[c]) for c in S) for S in itertools.combinations(range(k), t))
+            assert oracle.count(rp, ci, parent, oracle.colors(seed, n, k), ncolors=k).maps == \
+                math.factorial(t) * e_t
+
+
+def test_more_colors_estimate_unbiased():
+    # E[estimate] with k = |T| + 2 colors is still the number of copies (the star closed form)
+    rp, ci = sgcgen.er(40, 90, 21)
+    t = 3
+    truth = sum(math.comb(int(d), t - 1) for d in np.diff(rp))
+    e = oracle.estimate(rp, ci, sgcgen.star_tree(t), list(range(1, 3001)), ncolors=t + 2)
+    ests = np.array(e.estimates)
+    se = ests.std(ddof=1) / math.sqrt(len(ests))
+    assert abs(e.mean - truth) < 5 * se, (e.mean, truth, se)
+    assert oracle.colorful_probability(3, 5) == Fraction(5 * 4 * 3, 5 ** 3)
+
+
+def test_more_colors_rejects_too_few():
+    rp, ci = sgcgen.er(8, 14, 1)
+    with pytest.raises(Exception):
+        oracle.count(rp, ci, sgcgen.path_tree(4), oracle.colors(1, 8, 3), ncolors=3)
