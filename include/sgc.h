@@ -248,6 +248,35 @@ typedef struct sgc_tune_entry {
 sgc_status sgc_autotune(const sgc_graph* g, const sgc_template* t, const sgc_options* opt, sgc_tune_entry* out,
                         int32_t cap, int32_t* n);
 
+/* ---------------------------------------------------- iteration count -- */
+
+/*
+ * Colorings for an (eps, delta)-approximation of the copy count in the worst
+ * case: the lemma after Lemma 1 (Section 5.1) performs O(e^k log(1/delta) /
+ * eps^2) iterations; this returns ceil(e^k ln(1/delta) / eps^2), i.e. that
+ * bound with constant 1 (the paper gives none).  0 < eps, 0 < delta < 1,
+ * 1 <= k <= SGC_MAX_K; -1 on bad arguments.
+ */
+int64_t sgc_iterations_bound(int32_t k, double eps, double delta);
+
+/*
+ * Count colorings of template t until the estimate meets a relative
+ * (eps, delta) target empirically: after every chunk of colorings (seeds
+ * first_seed, first_seed + 1, ..., chunk = opt->batch or 32), with n colorings
+ * so far, mean m and sample standard deviation s of the per-coloring estimates
+ * (maps_i / |Aut(T)| * k^k / k!, Section 2.1), it stops once n >= min_iter and
+ * z * s / sqrt(n) <= eps * m, z the standard normal quantile at 1 - delta / 2
+ * (a normal-approximation confidence interval of half-width eps * m), or once
+ * n reaches max_iter (0: sgc_iterations_bound(k, eps, delta)).
+ *   estimate        out: m
+ *   n_used          out: n
+ *   rel_half_width  out (may be NULL): z * s / (sqrt(n) * m), 0 when m = 0
+ * Colorings are counted as by sgc_count with *opt (precision, batch, ...).
+ */
+sgc_status sgc_estimate(const sgc_graph* g, const sgc_template* t, double eps, double delta, uint64_t first_seed,
+                        int64_t min_iter, int64_t max_iter, const sgc_options* opt, double* estimate,
+                        int64_t* n_used, double* rel_half_width);
+
 /* --------------------------------------------------------------- serving -- */
 
 /*

@@ -99,6 +99,10 @@ SIGNATURES = {
                                       _P(sgc_options), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sgc_autotune": (ctypes.c_int, [_vp, _vp, _P(sgc_options), _P(sgc_tune_entry), ctypes.c_int32,
                                     _P(ctypes.c_int32)]),
+    "sgc_iterations_bound": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
+    "sgc_estimate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                                    ctypes.c_int64, _P(sgc_options), _P(ctypes.c_double), _P(ctypes.c_int64),
+                                    _P(ctypes.c_double)]),
     "sgc_count_device_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
     "sgc_server_create": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, _P(_vp)]),
     "sgc_server_submit": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int32,
@@ -261,6 +265,23 @@ def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:
         out.append({"kind": e.kind, "name": OP_KINDS.get(e.kind, "batch"), "t": e.t, "a": e.a, "p": e.p,
                     "batch": e.batch, "shapes": list(e.shapes[:m]), "ms": list(e.ms[:m]), "chosen": e.chosen})
     return out
+
+
+def sgc_iterations_bound(k: int, eps: float, delta: float) -> int:
+    """Worst-case colorings for an (eps, delta)-approximation: ceil(e^k ln(1/delta) / eps^2)."""
+    return int(lib().sgc_iterations_bound(k, eps, delta))
+
+
+def sgc_estimate(g: int, t: int, eps: float, delta: float, first_seed: int = 1, min_iter: int = 0,
+                 max_iter: int = 0, opt: sgc_options | None = None):
+    """Count colorings until the (eps, delta) stopping rule holds; returns (estimate, n_used, rel_half_width)."""
+    est = ctypes.c_double(0)
+    n = ctypes.c_int64(0)
+    rel = ctypes.c_double(0)
+    _check(lib().sgc_estimate(g, t, eps, delta, first_seed, min_iter, max_iter,
+                              ctypes.byref(opt) if opt is not None else None, ctypes.byref(est), ctypes.byref(n),
+                              ctypes.byref(rel)))
+    return float(est.value), int(n.value), float(rel.value)
 
 
 SGC_STATIC_WORKSPACE_BYTES = 64 << 20

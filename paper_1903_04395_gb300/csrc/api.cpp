@@ -2,6 +2,7 @@
 // and the host-side driver of sgc_count (batching colorings, workspace,
 // result read-back and the k^k/k! estimator of Section 2.1).
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -766,6 +767,62 @@ sgc_status sgc_count_many(const sgc_graph* g, int32_t n_templates, const sgc_tem
                           const uint64_t* seeds, int32_t n_iter, const sgc_options* opt, double* estimates,
                           double* colorful_maps) {
   return count_core(g, n_templates, templates, seeds, n_iter, opt, false, estimates, colorful_maps);
+}
+
+int64_t sgc_iterations_bound(int32_t k, double eps, double delta) {
+  if (k < 1 || k > SGC_MAX_K || !(eps > 0) || !(delta > 0) || !(delta < 1)) return -1;
+  const long double x = std::exp((long double)k) * std::log(1.0L / (long double)delta) / ((long double)eps * eps);
+  if (!(x < 9.0e18L)) return INT64_MAX;
+  return (int64_t)std::ceil(x);
+}
+
+sgc_status sgc_estimate(const sgc_graph* g, const sgc_template* t, double eps, double delta, uint64_t first_seed,
+                        int64_t min_iter, int64_t max_iter, const sgc_options* opt, double* estimate,
+                        int64_t* n_used, double* rel_half_width) {
+  sgc_status rc = check_handles(g, t);
+  if (rc != SGC_OK) return rc;
+  if (!estimate || !n_used) return fail(SGC_ERR_INVALID, "NULL argument");
+  if (!(eps > 0) || !(delta > 0) || !(delta < 1)) return fail(SGC_ERR_INVALID, "need eps > 0 and 0 < delta < 1");
+  if (min_iter < 0 || max_iter < 0) return fail(SGC_ERR_INVALID, "min_iter and max_iter must be >= 0");
+  const sgc_options o = resolve(opt);
+  const int64_t cap = max_iter > 0 ? max_iter : sgc_iterations_bound(t->k, eps, delta);
+  const int64_t chunk = o.batch > 0 ? o.batch : 32;
+  // z with P(|Z| > z) = delta for a standard normal Z: erfc(z / sqrt 2) = delta, by bisection
+  long double lo = 0.0L, hi = 40.0L;
+  for (int i = 0; i < 200; ++i) {
+    const long double mid = 0.5L * (lo + hi);
+    if (std::erfc(mid / std::sqrt(2.0L)) > (long double)delta) lo = mid; else hi = mid;
+  }
+  const long double z = 0.5L * (lo + hi);
+  long double scale = 1.0L;
+  for (int i = 1; i <= t->k; ++i) scale *= (long double)t->k / (long double)i;  // k^k / k!
+  scale /= (long double)t->aut;
+  long double sum = 0.0L, sum2 = 0.0L, half = 0.0L;
+  int64_t n = 0;
+  std::vector<uint64_t> seeds;
+  std::vector<double> maps;
+  while (n < cap) {
+    const int64_t m = std::min<int64_t>(chunk, cap - n);
+    seeds.resize((size_t)m);
+    maps.resize((size_t)m);
+    for (int64_t i = 0; i < m; ++i) seeds[(size_t)i] = first_seed + (uint64_t)(n + i);
+    if ((rc = count_core(g, 1, &t, seeds.data(), (int32_t)m, &o, false, nullptr, maps.data())) != SGC_OK) return rc;
+    for (double x : maps) {
+      const long double e = (long double)x * scale;
+      sum += e;
+      sum2 += e * e;
+    }
+    n += m;
+    const long double mean = sum / n;
+    const long double var = n > 1 ? std::max(0.0L, (sum2 - sum * mean) / (n - 1)) : 0.0L;
+    half = z * std::sqrt(var / n);
+    if (n >= min_iter && n > 1 && half <= (long double)eps * mean) break;
+  }
+  const long double mean = n > 0 ? sum / n : 0.0L;
+  *estimate = (double)mean;
+  *n_used = n;
+  if (rel_half_width) *rel_half_width = mean > 0 ? (double)(half / mean) : 0.0;
+  return SGC_OK;
 }
 
 sgc_status sgc_autotune(const sgc_graph* g, const sgc_template* t, const sgc_options* opt, sgc_tune_entry* out,

@@ -85,3 +85,15 @@ def test_null_arguments_rejected(built):
     assert L.sgc_template_create(3, None, None) == sgc.SGC_ERR_INVALID
     sgc.sgc_graph_destroy(None)
     sgc.sgc_template_destroy(None)
+
+
+def test_iterations_bound_is_the_lemma_count():
+    # the lemma after Lemma 1 (Section 5.1): O(e^k log(1/delta) / eps^2) colorings, constant 1
+    import math
+    sgc.build()
+    for k, eps, delta in [(5, 0.1, 0.05), (10, 0.05, 0.01), (1, 1.0, 0.5), (16, 0.2, 0.1)]:
+        want = math.ceil(math.exp(k) * math.log(1 / delta) / eps ** 2)
+        got = sgc.sgc_iterations_bound(k, eps, delta)
+        assert abs(got - want) <= 1, (k, eps, delta, got, want)
+    for bad in [(0, 0.1, 0.1), (17, 0.1, 0.1), (5, 0.0, 0.1), (5, 0.1, 0.0), (5, 0.1, 1.0)]:
+        assert sgc.sgc_iterations_bound(*bad) == -1
