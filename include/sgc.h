@@ -90,6 +90,9 @@ typedef struct sgc_options {
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
                           1 / 2 rows per lane (4..32 colorings per pass); ops it does not fit keep
                           theirs; 0 (default) = planner or autotuner */
+  int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
+                          |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have
+                          distinct colors; the estimate divides by k! / ((k - |T|)! k^|T|). */
 } sgc_options;
 
 /* Fill *opt with the defaults described above. */
@@ -182,7 +185,8 @@ sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_opt
  *                  (Steele, Lea and Flood 2014): x = mix(seed + (v+1) * 0x9E3779B97F4A7C15).
  *   opt            NULL for defaults
  *   estimate       out (host, may be NULL): mean over iterations of
- *                  maps_i / |Aut(T)| * k^k / k!
+ *                  maps_i / |Aut(T)| * k^k / k!  (with opt->colors = k > |T|:
+ *                  maps_i / |Aut(T)| * (k - |T|)! k^|T| / k!)
  *   colorful_maps  out (host, n_iter doubles, may be NULL): for each coloring
  *                  the number of colorful injective edge-preserving maps
  *                  T -> G, i.e. sum_v N(v, T, all colors) = |Aut(T)| * colorful copies.

@@ -28,6 +28,15 @@ sgc_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SGC_ERR_OOM : SGC_ERR_CUDA;
 }
 
+// 1 / P(a fixed copy of a t-vertex template is colorful) with k colors:
+// k^t (k - t)! / k! (k^k / k! for k = t, Section 2.1); colors = 0 means k = t
+long double inverse_colorful_probability(int t, int colors) {
+  const int k = colors > t ? colors : t;
+  long double x = 1.0L;
+  for (int i = 0; i < t; ++i) x *= (long double)k / (long double)(k - i);
+  return x;
+}
+
 int pow2_floor(int x) {
   int p = 1;
   while (p * 2 <= x) p *= 2;
@@ -119,7 +128,8 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
                         std::shared_ptr<PlanSet>* out) {
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
                           "/" + std::to_string(bmax) + (o.autotune ? "/tuned" : "") + "/s" +
-                          std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows);
+                          std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows) + "/c" +
+                          std::to_string(o.colors);
   for (auto& kv : g->plan_cache)
     if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
       *out = kv.second;
@@ -135,11 +145,11 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     return sh;
   };
   Plan p1;
-  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1);
+  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1, nullptr, o.colors);
   if (rc != SGC_OK) return rc;
   if (forced) {
     const std::vector<int> sh = forced_shapes(p1);
-    if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh)) != SGC_OK) return rc;
+    if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh, o.colors)) != SGC_OK) return rc;
   }
   if (p1.ws_bytes > mem_limit)
     return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) + " bytes of device workspace, limit " +
@@ -156,11 +166,11 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   set->bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
-    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb);
+    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors);
     if (rc != SGC_OK) return rc;
     if (forced) {
       const std::vector<int> sh = forced_shapes(pb);
-      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh)) != SGC_OK) return rc;
+      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh, o.colors)) != SGC_OK) return rc;
     }
     if (pb.ws_bytes > mem_limit) break;
     set->by_batch[b] = std::move(pb);
@@ -262,7 +272,7 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
       for (size_t i = 0; i < nops; ++i)
         if (!cands[i].empty()) shapes[i] = cands[i][std::min(c, cands[i].size() - 1)];
       Plan p;
-      sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes);
+      sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes, o.colors);
       if (rc != SGC_OK) return rc;
       TimedPass tp;
       if ((rc = time_pass(g, p, pool, st, &tp)) != SGC_OK) return rc;
@@ -302,7 +312,7 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
       report.push_back(te);
     }
     Plan tuned;
-    sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best);
+    sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best, o.colors);
     if (rc != SGC_OK) return rc;
     set->by_batch[b] = std::move(tuned);
     const double per = pass_ms / b;
@@ -446,8 +456,11 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
   if (device_io && n_iter > 0 && n_t > 0 && !maps_out) return fail(SGC_ERR_INVALID, "colorful_maps is NULL");
   const sgc_options o = resolve(opt_in);
   if (o.precision != SGC_FP32 && o.precision != SGC_FP64) return fail(SGC_ERR_INVALID, "unknown precision");
-  for (int32_t j = 0; j < n_t; ++j)
+  for (int32_t j = 0; j < n_t; ++j) {
     if (o.root >= ts[j]->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
+    if (o.colors != 0 && (o.colors < ts[j]->k || o.colors > SGC_MAX_K))
+      return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
+  }
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
   if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmDirectBPriv)
     return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..13");
@@ -605,9 +618,7 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
   if (maps_out) std::memcpy(maps_out, host_maps.data(), sizeof(double) * total);
   if (estimates)
     for (int32_t j = 0; j < n_t; ++j) {
-      const int k = ts[j]->k;
-      long double scale = 1.0L;
-      for (int i = 1; i <= k; ++i) scale *= (long double)k / (long double)i;  // k^k / k!
+      const long double scale = inverse_colorful_probability(ts[j]->k, o.colors);
       long double s = 0;
       for (int32_t i = 0; i < n_iter; ++i) s += (long double)host_maps[(size_t)j * n_iter + (size_t)i];
       estimates[j] = (double)(s / (long double)n_iter / (long double)ts[j]->aut * scale);
@@ -633,6 +644,7 @@ void sgc_options_init(sgc_options* opt) {
   opt->autotune = 0;
   opt->spmm_shape = 0;
   opt->ema_rows = 0;
+  opt->colors = 0;
 }
 
 const char* sgc_last_error(void) { return g_last_error.c_str(); }
@@ -738,7 +750,7 @@ sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_opt
   if (o.root >= t->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
   Plan p;
   const int b = pow2_floor(std::max(1, std::min(32, o.batch > 0 ? o.batch : 1)));
-  if ((rc = make_plan(g, t, o.precision, o.root, -1, b, false, &p)) != SGC_OK) return rc;
+  if ((rc = make_plan(g, t, o.precision, o.root, -1, b, false, &p, nullptr, o.colors)) != SGC_OK) return rc;
   out->root = p.root;
   out->n_tables = p.n_tables;
   out->n_spmm = p.n_spmm;
@@ -794,9 +806,9 @@ sgc_status sgc_estimate(const sgc_graph* g, const sgc_template* t, double eps, d
     if (std::erfc(mid / std::sqrt(2.0L)) > (long double)delta) lo = mid; else hi = mid;
   }
   const long double z = 0.5L * (lo + hi);
-  long double scale = 1.0L;
-  for (int i = 1; i <= t->k; ++i) scale *= (long double)t->k / (long double)i;  // k^k / k!
-  scale /= (long double)t->aut;
+  if (o.colors != 0 && (o.colors < t->k || o.colors > SGC_MAX_K))
+    return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
+  const long double scale = inverse_colorful_probability(t->k, o.colors) / (long double)t->aut;
   long double sum = 0.0L, sum2 = 0.0L, half = 0.0L;
   int64_t n = 0;
   std::vector<uint64_t> seeds;

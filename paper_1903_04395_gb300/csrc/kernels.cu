@@ -1238,6 +1238,32 @@ __global__ void __launch_bounds__(kBlock) k_final_leaf(const T* __restrict__ P, 
   }
 }
 
+// More colors than template vertices (Section 2.1, k >= |T|): maps_b = sum_v of
+// all entries of the root table row (every |T|-subset of colors containing
+// c(v)); summed like k_final: the row in the table type, vertices in FP64,
+// per-block partials per coloring.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_final_rows(const T* __restrict__ M, int64_t ld, int cols, int64_t rows,
+                                                       int lb, double* __restrict__ partials) {
+  __shared__ double tacc[kBlock];
+  const int batch = 1 << lb;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;  // multiple of batch
+  double acc = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S) {
+    const T* m = M + (((row >> lb) * ld) << lb) + (row & (batch - 1));
+    T part = T(0);
+    for (int i = 0; i < cols; ++i) part += m[(int64_t)i << lb];
+    acc += (double)part;
+  }
+  tacc[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < batch) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += batch) s += tacc[i];
+    partials[(int64_t)blockIdx.x * batch + threadIdx.x] = s;
+  }
+}
+
 __global__ void k_final_sum(const double* __restrict__ partials, int nblocks, int batch, const ScaleState* st_a,
                             const ScaleState* st_p, int fp32, double* __restrict__ out) {
   const int b = threadIdx.x;
@@ -1619,6 +1645,12 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
       case OP_FINAL_LEAF:
         k_final_leaf<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p, rows,
                                                               lb, partials);
+        k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
+        nk += 2;
+        break;
+      case OP_FINAL_SUM:
+        k_final_rows<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
+                                                              (int)op.cols_p, rows, lb, partials);
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
         nk += 2;
         break;

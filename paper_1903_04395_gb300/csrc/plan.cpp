@@ -492,17 +492,24 @@ static int64_t spmm_cols_per_lane(int batch, int64_t cols_p) {
   return (cols_p + lanes_per_col - 1) / lanes_per_col;
 }
 
+// `colors` = number of colors k >= |T| (0: k = |T|).  Section 2.1 draws colors
+// from k >= |T|; with k > |T| the root table keeps every (|T|-1)-subset of the
+// other colors and the last op sums its entries (OP_FINAL_SUM) instead of
+// evaluating the single full color set.
 static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy,
-                     int batch, bool build_tabs, Plan* P, const std::vector<int>* shapes = nullptr) {
+                     int batch, bool build_tabs, Plan* P, const std::vector<int>* shapes = nullptr,
+                     int colors = 0) {
   Rooted R;
   root_tree(t, root, &R);
   Builder B(R, policy);
   B.build(root, 0);
-  const int k = t->k;
+  const int tk = t->k;                          // template vertices
+  const int k = colors > tk ? colors : tk;      // colors
   const int K = k - 1;
   ColorIndex cr(K);
 
   P->k = k;
+  P->t_size = tk;
   P->root = root;
   P->policy = policy;
   P->batch = batch;
@@ -647,7 +654,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       P->ops.push_back(op);
     }
     // ---- the combine step
-    const bool final = C.size == k;
+    const bool final = C.size == tk && tk == k;  // the single full color set
     if (A.a < 0 && !final) {
       // single-vertex active child: M_s(v, S + c(v)) = P(v, S), the same numbers
       table_buf[c] = pbuf[C.p];
@@ -730,6 +737,26 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
     P->n_ema++;
     use_buf(P, op.in_a, idx);
     use_buf(P, op.in_p, idx);
+    P->ops.push_back(op);
+  }
+  if (tk < k) {
+    // more colors than template vertices: sum the root table over all its color sets
+    int rc = -1;
+    for (size_t c = 0; c < B.cls.size(); ++c)
+      if (B.cls[c].size == tk) rc = (int)c;
+    PlanOp op{};
+    op.kind = OP_FINAL_SUM;
+    op.t = tk;
+    op.in_p = table_buf[rc];
+    op.state_p = table_state[rc];
+    op.cols_p = table_w[rc];
+    op.ld_p = table_ld[rc];
+    op.out = P->buf_partials;
+    op.alg_bytes = (double)elem * nv * batch * (double)op.cols_p;
+    op.alg_flops = nv * batch * (double)op.cols_p;
+    P->est_bytes += nv * (double)op.cols_p * elem;
+    P->est_cost += nv * (double)op.cols_p * elem / bw;
+    use_buf(P, op.in_p, (int)P->ops.size());
     P->ops.push_back(op);
   }
   P->n_states = n_states;
@@ -833,7 +860,9 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
 }
 
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out, const std::vector<int>* shapes) {
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes, int colors) {
+  if (colors != 0 && (colors < t->k || colors > SGC_MAX_K))
+    return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   if (root >= t->k) return fail(SGC_ERR_INVALID, "options.root is not a template vertex");
   int best_root = -1, best_policy = 0;
   double best_cost = 0;
@@ -843,7 +872,7 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
     for (int pol = 0; pol < 2; ++pol) {
       if (policy >= 0 && pol != policy) continue;
       Plan P;
-      plan_for(g, t, precision, r, pol, 1, false, &P);
+      plan_for(g, t, precision, r, pol, 1, false, &P, nullptr, colors);
       if (best_root < 0 || P.est_cost < best_cost * 0.999 ||
           (P.est_cost <= best_cost * 1.001 && P.ws_bytes < best_ws)) {
         best_root = r;
@@ -853,8 +882,8 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
       }
     }
   }
-  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out, shapes);
-  if (build_tabs && !tables_in_range(*out, t->k)) return fail(SGC_ERR_INTERNAL, "index table out of range");
+  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out, shapes, colors);
+  if (build_tabs && !tables_in_range(*out, out->k)) return fail(SGC_ERR_INTERNAL, "index table out of range");
   return SGC_OK;
 }
 

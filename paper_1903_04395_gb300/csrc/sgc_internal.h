@@ -129,6 +129,7 @@ enum OpKind : int32_t {
   OP_EMA = 4,        // eMA over the split table (a single-vertex active child needs none)
   OP_FINAL_LEAF = 5, // last step, single-vertex active child, fused with the vertex sum
   OP_FINAL = 6,      // last step, general, fused with the vertex sum
+  OP_FINAL_SUM = 7,  // more colors than template vertices: sum of the root table's entries
 };
 
 struct PlanBuffer {
@@ -173,7 +174,8 @@ struct PlanOp {
 };
 
 struct Plan {
-  int k = 0, root = 0, batch = 1, precision = SGC_FP32, policy = 0;
+  int k = 0, root = 0, batch = 1, precision = SGC_FP32, policy = 0;  // k = number of colors
+  int t_size = 0;            // template vertices (<= k)
   int elem = 4;              // bytes per table entry
   int64_t rows = 0;          // n_act * batch
   std::vector<PlanBuffer> bufs;
@@ -222,9 +224,9 @@ inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4
 // cost model choose; batch is the number of colorings per pass.  Index tables
 // are only built when build_tabs is set.  `shapes`, when given, holds one
 // launch-shape code per op index (0 = default); codes that do not fit the
-// op (shared memory, form) are ignored.
+// op (shared memory, form) are ignored.  colors = number of colors (0: |T|).
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr);
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr, int colors = 0);
 
 // The launch shapes worth timing for op `i` of plan p (empty: nothing to choose).
 std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& p, int i);
@@ -232,6 +234,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& p, int i);
 uint64_t automorphisms(const sgc_template* t);
 
 int pow2_floor(int x);
+long double inverse_colorful_probability(int t, int colors);
 sgc_options resolve(const sgc_options* opt);
 struct PlanSet;
 // Plans for every power-of-two batch up to bmax (capped for SpMM occupancy) whose
