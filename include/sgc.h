@@ -86,7 +86,7 @@ typedef struct sgc_options {
                           lane), 10 bucketed specialised for the batch; ops it does not fit keep
                           theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
-  int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8 or 4 rows staged column-major per
+  int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
                           1 / 2 rows per lane (4..32 colorings per pass); ops it does not fit keep
                           theirs; 0 (default) = planner or autotuner */

@@ -1012,16 +1012,31 @@ __global__ void __launch_bounds__(kBlock) k_ema(
   for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
     const int nr = (int)(rows - r0 < R ? rows - r0 : R);
     __syncthreads();
-    for (int i = threadIdx.x; i < R * ca; i += blockDim.x) {
-      const int c = i / R, rr = i - c * R;
-      const int64_t r = r0 + rr;
-      sm[c * RS + rr] = rr < nr ? Ma[(((r >> lb) * lda + c) << lb) + (r & bmask)] : T(0);
-    }
-    for (int i = threadIdx.x; i < R * cp; i += blockDim.x) {
-      const int c = i / R, rr = i - c * R;
-      const int64_t r = r0 + rr;
-      sm[(ca + c) * RS + rr] = rr < nr ? P[(((r >> lb) * ldp + c) << lb) + (r & bmask)] : T(0);
-    }
+    // staging: eight loads per thread in flight before their stores (wide rows stage
+    // tens of KB per block, which a load-store-load loop would serialise on latency)
+    auto stage = [&](const T* __restrict__ src, int64_t ld, int cols, int col0) {
+      const int total = R * cols;
+      for (int i0 = threadIdx.x; i0 < total; i0 += 8 * (int)blockDim.x) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * (int)blockDim.x;
+          const int c = i / R, rr = i - c * R;
+          const int64_t r = r0 + rr;
+          v[u] = (i < total && rr < nr) ? src[(((r >> lb) * ld + c) << lb) + (r & bmask)] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * (int)blockDim.x;
+          if (i < total) {
+            const int c = i / R, rr = i - c * R;
+            sm[(col0 + c) * RS + rr] = v[u];
+          }
+        }
+      }
+    };
+    stage(Ma, lda, ca, 0);
+    stage(P, ldp, cp, ca);
     __syncthreads();
     const T* base = sm + r;
     for (int S = warp * NSUB + sub; S < ldt; S += nwarp * NSUB) {

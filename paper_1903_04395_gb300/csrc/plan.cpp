@@ -238,14 +238,18 @@ struct TabKey {  // (kind, t, a, eMA rows) of an index table
 // eMA block shape: rows staged per block so that both input rows fit in
 // shared memory as [column][row] with row stride rows+1; 64 rows (two per
 // lane) when possible.
+// Rows an eMA block stages: the most that keep a block within 72 KB of shared
+// memory (three blocks per SM), else the most that fit at all.
 void ema_shape(int64_t ca, int64_t cp, int elem, int smem_cap, int* rows, int* rpl) {
   const int64_t per = (ca + cp) * elem;
   const int cands[] = {64, 32, 16, 8, 4, 2, 1};
-  for (int r : cands) {
-    if (per * (r + 1) <= smem_cap) {
-      *rows = r;
-      *rpl = r == 64 ? 2 : 1;
-      return;
+  for (int64_t cap : {std::min<int64_t>(72 * 1024, smem_cap), (int64_t)smem_cap}) {
+    for (int r : cands) {
+      if (per * (r + 1) <= cap) {
+        *rows = r;
+        *rpl = r == 64 ? 2 : 1;
+        return;
+      }
     }
   }
   *rows = 0;
@@ -704,7 +708,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       const bool sym = A.size - 1 == Pc.size && table_buf[C.a] == pbuf[C.p];
       // default: vertex tiles when they fit (measured faster on R-MAT 20), else rows
       op.ema_vrpl = ema_vertex_fits(batch, 1, op.ld_a, op.ld_p, sym, elem, smem_cap) ? 1 : 0;
-      if ((shape == 64 || shape == 32 || shape == 16 || shape == 8 || shape == 4) &&
+      if ((shape == 64 || shape == 32 || shape == 16 || shape == 8 || shape == 4 || shape == 2 || shape == 1) &&
           (op.cols_a + op.cols_p) * elem * (shape + 1) <= smem_cap) {
         op.ema_rows = shape;
         op.ema_rpl = shape == 64 ? 2 : 1;
@@ -850,8 +854,8 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       c.push_back(kShapeSpmmRing4);
     }
   } else if (op.kind == OP_EMA) {
-    for (int r : {64, 32, 16, 8})
-      if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap) c.push_back(r);
+    for (int r : {64, 32, 16, 8, 4, 2, 1})
+      if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap && c.size() < 5) c.push_back(r);
     for (int v : {1, 2})
       if (ema_vertex_fits(P.batch, v, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap)) c.push_back(100 + v);
   }

@@ -108,7 +108,7 @@ def test_every_spmm_shape(precision, spmm_shape):
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
-@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 101, 102])
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_ema_shape(ema_rows, precision):
     sgc.build()
