@@ -287,11 +287,13 @@ sgc_status sgc_estimate(const sgc_graph* g, const sgc_template* t, double eps, d
  * A counting server over one device-resident graph with continuous batching
  * (the paper has no counterpart; it serves many color-coding queries on one
  * graph).  Requests (template, colorings) queue on the host; a scheduler thread
- * admits them in arrival order - looking past a request that does not fit yet -
- * whenever their device workspace fits in the free part of `mem_budget` bytes
+ * admits them - of the first 8 queued, the shortest by the planner's cost model
+ * that fits; the oldest is overtaken at most 8 times - whenever their device
+ * workspace fits in the free part of `mem_budget` bytes
  * (allocated once, at creation) and one of `max_inflight` execution slots is
  * free.  Each admitted request runs its DP passes on its own stream, so requests
- * overlap on the GPU.  Results are those of sgc_count for the same seeds and
+ * overlap on the GPU; the stream's priority follows the request's estimated
+ * device time (shorter requests get higher priorities).  Results are those of sgc_count for the same seeds and
  * precision (FP32 within the FP32 tolerance: a request's batch size may differ).
  * The graph and every submitted template must outlive the server.
  */

@@ -1,11 +1,16 @@
 // server.cpp - a counting server over one device-resident graph, with
 // continuous batching: requests (template, colorings) queue on the host; a
-// scheduler thread admits them, in arrival order with a short look-ahead, as
-// soon as their device workspace fits in the free part of a fixed memory
-// budget and an execution slot is free; every admitted request runs its
-// passes on its own stream, so requests overlap on the GPU; completions are
+// scheduler thread admits them as soon as their device workspace fits in the
+// free part of a fixed memory budget and an execution slot is free - of the
+// first few queued requests the shortest (estimated device time) first, the
+// head of the queue overtaken a bounded number of times; every admitted
+// request runs its passes on its own stream, so requests overlap on the GPU; completions are
 // detected with events, results copied back, memory returned, and the wait
 // of the submitter released.  Latency = completion time - submission time.
+// A request's stream takes a priority from its estimated device time (the
+// planner's cost model times its colorings): shorter requests get higher
+// priorities, so the GPU's block scheduler lets them through while long ones
+// run (no request is ever held back: priorities only order ready blocks).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,6 +40,8 @@ struct Request {
   std::map<int, const uint32_t*> tabs;
   int64_t off = 0, bytes = 0;  // workspace range in the arena
   int slot = -1;
+  cudaStream_t st = nullptr;   // the slot's stream at this request's priority
+  int bypassed = 0;            // admissions that overtook this request at the head
   // result
   bool finished = false;
   sgc_status status = SGC_OK;
@@ -55,7 +62,7 @@ struct sgc_server {
   int max_inflight = 0;
   char* arena = nullptr;
   std::vector<Range> free_ranges;
-  std::vector<cudaStream_t> streams;
+  std::vector<std::vector<cudaStream_t>> streams;  // [priority level][slot], level 0 highest
   std::vector<cudaEvent_t> events;
   std::vector<std::shared_ptr<Request>> slots;  // in flight, by slot
   std::deque<std::shared_ptr<Request>> pending;
@@ -75,7 +82,8 @@ struct sgc_server {
 namespace sgc {
 namespace {
 
-constexpr int kLookahead = 8;  // pending requests examined past a head that does not fit
+constexpr int kLookahead = 8;  // queued requests considered for admission
+constexpr int kMaxBypass = 8;  // admissions that may overtake the head of the queue
 
 int64_t take_range(sgc_server* s, int64_t need) {
   need = (need + 255) / 256 * 256;
@@ -92,6 +100,13 @@ int64_t take_range(sgc_server* s, int64_t need) {
     }
   }
   return -1;
+}
+
+bool fits(const sgc_server* s, int64_t need) {
+  need = (need + 255) / 256 * 256;
+  for (const Range& r : s->free_ranges)
+    if (r.len >= need) return true;
+  return false;
 }
 
 void give_range(sgc_server* s, int64_t off, int64_t len) {
@@ -128,10 +143,27 @@ void finish(sgc_server* s, const std::shared_ptr<Request>& r, sgc_status st, con
   }
 }
 
-// Enqueue all passes of `r` on slot `slot`'s stream; the caller holds s->mu.
+// Estimated device seconds of a request: the planner's cost model per coloring
+// times its colorings.
+double request_cost(const Request& r) {
+  const Plan& top = r.plans->by_batch.at(r.plans->bfit);
+  return top.est_cost * (double)r.seeds.size();
+}
+
+// Priority level of a request: level 0 (highest) below ~1 ms of estimated
+// device time, one level lower for every factor of 4 more.
+int priority_level(const sgc_server* s, const Request& r) {
+  const double est_ms = 1e3 * request_cost(r);
+  int level = 0;
+  for (double x = 1.0; est_ms > x && level + 1 < (int)s->streams.size(); x *= 4.0) ++level;
+  return level;
+}
+
+// Enqueue all passes of `r` on slot `slot`'s stream at its priority; the caller holds s->mu.
 sgc_status launch(sgc_server* s, const std::shared_ptr<Request>& r, int slot) {
   const sgc_graph* g = s->g;
-  cudaStream_t st = s->streams[slot];
+  r->st = s->streams[(size_t)priority_level(s, *r)][(size_t)slot];
+  cudaStream_t st = r->st;
   char* base = s->arena + r->off;
   const Plan& top = r->plans->by_batch.at(r->plans->bfit);
   char* ws = base;
@@ -194,8 +226,8 @@ void scheduler(sgc_server* s) {
             s->arena + r->off + (top.ws_bytes + 255) / 256 * 256 + (int64_t)r->seeds.size() * 8);
         r->maps.assign(r->seeds.size(), 0.0);
         cudaError_t e = cudaMemcpyAsync(r->maps.data(), d_maps, sizeof(double) * r->maps.size(),
-                                        cudaMemcpyDeviceToHost, s->streams[slot]);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->streams[slot]);
+                                        cudaMemcpyDeviceToHost, r->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->st);
         if (e == cudaSuccess) {
           const int k = r->t->k;
           long double scale = 1.0L, sum = 0;
@@ -219,16 +251,20 @@ void scheduler(sgc_server* s) {
       for (auto& r : s->slots) busy = busy || (bool)r;
       if (!busy) break;
     }
-    // admissions: arrival order, looking past a head that does not fit yet
-    if (!s->stop) {
-      for (int look = 0; look < kLookahead && look < (int)s->pending.size();) {
-        int slot = -1;
-        for (int i = 0; i < s->max_inflight; ++i)
-          if (!s->slots[i]) {
-            slot = i;
-            break;
-          }
-        if (slot < 0) break;
+    // admissions: among the first kLookahead queued requests, the shortest (estimated
+    // device time) that fits in a free slot and the free budget; the head of the queue
+    // is bypassed at most kMaxBypass times before it goes first
+    while (!s->stop && !s->pending.empty()) {
+      int slot = -1;
+      for (int i = 0; i < s->max_inflight; ++i)
+        if (!s->slots[i]) {
+          slot = i;
+          break;
+        }
+      if (slot < 0) break;
+      // settle the window: trivial requests finish at once, the others get their plans
+      bool restart = false;
+      for (int look = 0; look < kLookahead && look < (int)s->pending.size(); ++look) {
         std::shared_ptr<Request> r = s->pending[look];
         if (r->t->k == 1 || s->g->n_act == 0) {
           // no pass needed: every vertex is a map (k = 1) or nothing maps (no edges)
@@ -238,7 +274,8 @@ void scheduler(sgc_server* s) {
           finish(s, r, SGC_OK, "");
           s->pending.erase(s->pending.begin() + look);
           s->cv_done.notify_all();
-          continue;
+          restart = true;
+          break;
         }
         if (!r->plans) {
           // plan without holding the server lock; the queue may change meanwhile
@@ -248,45 +285,60 @@ void scheduler(sgc_server* s) {
           std::string err = rc != SGC_OK ? std::string(sgc_last_error()) : std::string();
           lock.lock();
           auto pos = std::find(s->pending.begin(), s->pending.end(), r);
-          if (s->stop || pos == s->pending.end()) break;  // cancelled while planning
-          look = (int)(pos - s->pending.begin());
+          if (s->stop || pos == s->pending.end()) {  // cancelled while planning
+            restart = true;
+            break;
+          }
+          if (rc == SGC_OK) {
+            r->bytes = request_bytes(*r);
+            if (r->bytes > s->budget) {
+              rc = SGC_ERR_OOM;
+              err = "request needs " + std::to_string(r->bytes) + " bytes, budget " + std::to_string(s->budget);
+            }
+          }
           if (rc != SGC_OK) {
             finish(s, r, rc, err);
             s->pending.erase(pos);
             s->cv_done.notify_all();
-            continue;
+            restart = true;
+            break;
           }
         }
-        r->bytes = request_bytes(*r);
-        if (r->bytes > s->budget) {
-          finish(s, r, SGC_ERR_OOM, "request needs " + std::to_string(r->bytes) + " bytes, budget " +
-                                        std::to_string(s->budget));
-          s->pending.erase(s->pending.begin() + look);
-          s->cv_done.notify_all();
-          continue;
-        }
-        const int64_t off = take_range(s, r->bytes);
-        if (off < 0) {
-          ++look;  // does not fit now; a later, smaller request may
-          continue;
-        }
-        r->off = off;
-        r->slot = slot;
-        r->t_start = Clock::now();
-        s->pending.erase(s->pending.begin() + look);
-        sgc_status rc = launch(s, r, slot);
-        if (rc != SGC_OK) {
-          cudaStreamSynchronize(s->streams[slot]);
-          give_range(s, r->off, r->bytes);
-          finish(s, r, rc, sgc_last_error());
-          s->cv_done.notify_all();
-          continue;
-        }
-        s->slots[slot] = r;
-        int inflight = 0;
-        for (auto& x : s->slots) inflight += x ? 1 : 0;
-        s->peak_inflight = std::max(s->peak_inflight, inflight);
       }
+      if (restart) continue;
+      // choose
+      const std::shared_ptr<Request> head = s->pending.front();
+      int best = -1;
+      double best_cost = 0;
+      const int window = head->bypassed >= kMaxBypass ? 1 : std::min<int>(kLookahead, (int)s->pending.size());
+      for (int look = 0; look < window; ++look) {
+        const Request& r = *s->pending[look];
+        if (!fits(s, r.bytes)) continue;
+        const double cost = request_cost(r);
+        if (best < 0 || cost < best_cost) {
+          best = look;
+          best_cost = cost;
+        }
+      }
+      if (best < 0) break;  // nothing fits until running requests finish
+      if (best != 0) head->bypassed++;
+      std::shared_ptr<Request> r = s->pending[best];
+      r->off = take_range(s, r->bytes);
+      r->slot = slot;
+      r->t_start = Clock::now();
+      s->pending.erase(s->pending.begin() + best);
+      sgc_status rc = launch(s, r, slot);
+      if (rc != SGC_OK) {
+        cudaStreamSynchronize(r->st);
+        give_range(s, r->off, r->bytes);
+        finish(s, r, rc, sgc_last_error());
+        s->cv_done.notify_all();
+        continue;
+      }
+      s->slots[slot] = r;
+      int inflight = 0;
+      for (auto& x : s->slots) inflight += x ? 1 : 0;
+      s->peak_inflight = std::max(s->peak_inflight, inflight);
     }
     bool any_inflight = false;
     for (auto& x : s->slots) any_inflight = any_inflight || (bool)x;
@@ -330,13 +382,16 @@ sgc_status sgc_server_create(const sgc_graph* g, int64_t mem_budget, int32_t max
                                  cudaGetErrorString(e));
   }
   s->free_ranges.push_back({0, s->budget});
-  s->streams.resize(max_inflight);
+  int least = 0, greatest = 0;  // numerically lower = higher priority
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int levels = std::max(1, least - greatest + 1);
+  s->streams.assign((size_t)levels, std::vector<cudaStream_t>((size_t)max_inflight, nullptr));
   s->events.resize(max_inflight);
   s->slots.resize(max_inflight);
-  for (int i = 0; i < max_inflight; ++i) {
-    cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
-  }
+  for (int l = 0; l < levels; ++l)
+    for (int i = 0; i < max_inflight; ++i)
+      cudaStreamCreateWithPriority(&s->streams[(size_t)l][(size_t)i], cudaStreamNonBlocking, greatest + l);
+  for (int i = 0; i < max_inflight; ++i) cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming);
   s->worker = std::thread(scheduler, s);
   *out = s;
   return SGC_OK;
@@ -415,9 +470,12 @@ void sgc_server_destroy(sgc_server* s) {
   s->cv_done.notify_all();
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->g->device);
+  for (auto& level : s->streams)
+    for (cudaStream_t st : level) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   for (int i = 0; i < s->max_inflight; ++i) {
-    cudaStreamSynchronize(s->streams[i]);
-    cudaStreamDestroy(s->streams[i]);
     cudaEventDestroy(s->events[i]);
   }
   cudaFree(s->arena);
