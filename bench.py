@@ -44,6 +44,11 @@ WORKLOADS = {
                     desc="Erdos-Renyi G(n=500,000, m=6,000,000; seed 1) and R-MAT scale 20; Pruefer trees of "
                          "5, 7, 8, 10, 11, 12 vertices (seeds 1000+size), 256 colorings each, all templates of a "
                          "graph in one sgc_count_many call = one CUDA-graph launch; autotuned launch shapes"),
+    "ablation": dict(scale=16, templates=[("spider10", ("spider", [3, 3, 3])), ("pruefer8", ("pruefer", 8, 1008))],
+                     batch=8, fp64=False, steps=3, warmup=3,
+                     desc="pruning ablation: the same colorings counted with the SpMM + eMA path (neighbour sums "
+                          "once per passive color set, Eq. 2) and in Algorithm 1's loop order (sums taken again per "
+                          "color set and split), R-MAT scale 16"),
     "rmat21-trees": dict(scale=21, templates=[("path12", ("path", 12)), ("pruefer13", ("pruefer", 13, 7)),
                                               ("pruefer15", ("pruefer", 15, 9))], batch=4, fp64=False,
                          desc="R-MAT scale 21 (edge factor 16, a=.57 b=.19 c=.19, seed 1); 12-vertex path, "
@@ -363,6 +368,52 @@ def run_serving(args, wl, rank, world, local):
         print(json.dumps(res), flush=True)
 
 
+def run_ablation(args, wl, rank, world, local):
+    """Pruned (SpMM + eMA) against unpruned (Algorithm 1 order) on the same colorings: the speed-up of
+    the pruning of Eq. 2 on the GPU (the paper reports it on CPUs against FASCIA)."""
+    import torch
+    import paper_1903_04395_gb300 as sgc
+    torch.cuda.set_device(local)
+    if rank == 0:
+        sgc.build()
+    sgc.lib()
+    stream = torch.cuda.Stream()
+    rp, ci = make_graph(wl)
+    g = sgc.Graph(rp, ci)
+    B, K, W = wl["batch"], args.steps, args.warmup
+    out = []
+    for name, spec in wl["templates"]:
+        t = sgc.Template(make_parent(spec))
+        row = {"template": name}
+        for mode in ("pruned", "unpruned"):
+            opt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream,
+                                       unpruned=1 if mode == "unpruned" else 0)
+            seeds = np.arange(1, 1 + B * (W + K), dtype=np.uint64)
+            for s in range(W):
+                sgc.sgc_count(g.handle, t.handle, seeds[s * B:(s + 1) * B], opt)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            maps = []
+            e0.record(stream)
+            for s in range(W, W + K):
+                maps.append(sgc.sgc_count(g.handle, t.handle, seeds[s * B:(s + 1) * B], opt)[1].copy())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[mode] = {"colorings_per_s": K * B / (e0.elapsed_time(e1) / 1e3), "maps_first": float(maps[0][0])}
+        row["speedup"] = row["pruned"]["colorings_per_s"] / row["unpruned"]["colorings_per_s"]
+        row["same_counts"] = abs(row["pruned"]["maps_first"] - row["unpruned"]["maps_first"]) <= \
+            1e-5 * abs(row["pruned"]["maps_first"])
+        out.append(row)
+    res = {"metric": METRIC, "value": out[0]["pruned"]["colorings_per_s"], "unit": "colorings/s", "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": 1e3 * B / out[0]["pruned"]["colorings_per_s"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "ablation", "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
+                      % wl["scale"], "colorings_per_step": B},
+           "ablation": out}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def batched_graphs():
     """The batched workload's graphs: (name, row_ptr, col_idx)."""
     import sgcgen
@@ -571,6 +622,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, wl, rank, world, local)
+        return
+    if args.workload == "ablation":
+        run_ablation(args, wl, rank, world, local)
         return
 
     import torch

@@ -93,6 +93,9 @@ typedef struct sgc_options {
   int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
                           |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have
                           distinct colors; the estimate divides by k! / ((k - |T|)! k^|T|). */
+  int32_t unpruned;    /* 1 = ablation of the pruning (Eq. 2, Section 4.2): every combine in
+                          Algorithm 1's loop order, the neighbour sum taken again for each color
+                          set and split (no SpMM); same results, far more work.  0 (default). */
 } sgc_options;
 
 /* Fill *opt with the defaults described above. */

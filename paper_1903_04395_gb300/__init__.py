@@ -39,7 +39,7 @@ class sgc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("batch", ctypes.c_int32), ("mem_limit", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("root", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("spmm_shape", ctypes.c_int32), ("ema_rows", ctypes.c_int32),
-                ("colors", ctypes.c_int32)]
+                ("colors", ctypes.c_int32), ("unpruned", ctypes.c_int32)]
 
 
 class sgc_graph_stats(ctypes.Structure):
@@ -74,7 +74,7 @@ class sgc_tune_entry(ctypes.Structure):
                 ("shapes", ctypes.c_int32 * 8), ("ms", ctypes.c_double * 8)]
 
 
-OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 4: "ema", 5: "final_leaf", 6: "final", 7: "final_sum"}
+OP_KINDS = {0: "color", 1: "hist", 2: "spmm", 4: "ema", 5: "final_leaf", 6: "final", 7: "final_sum", 8: "unpruned"}
 
 # exported symbols with their ctypes signatures (restype, argtypes)
 _P = ctypes.POINTER
@@ -149,11 +149,12 @@ def _i32(a):
 # ----------------------------------------------------------- C-named calls --
 
 def sgc_options_init(precision=SGC_FP32, batch=0, mem_limit=0, stream=None, root=-1, use_graph=1,
-                     autotune=0, spmm_shape=0, ema_rows=0, colors=0) -> sgc_options:
+                     autotune=0, spmm_shape=0, ema_rows=0, colors=0, unpruned=0) -> sgc_options:
     o = sgc_options()
     lib().sgc_options_init(ctypes.byref(o))
     o.precision, o.batch, o.mem_limit, o.root, o.use_graph = precision, batch, mem_limit, root, use_graph
     o.autotune, o.spmm_shape, o.ema_rows, o.colors = autotune, spmm_shape, ema_rows, colors
+    o.unpruned = unpruned
     o.stream = stream
     return o
 
@@ -443,10 +444,11 @@ class CountResult:
 
 def count(graph: Graph, template: Template, seeds, precision: str = "fp32", batch: int = 0, root: int = -1,
           mem_limit: int = 0, use_graph: bool = True, autotune: bool = False, spmm_shape: int = 0,
-          ema_rows: int = 0, colors: int = 0) -> CountResult:
+          ema_rows: int = 0, colors: int = 0, unpruned: bool = False) -> CountResult:
     opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root,
                            mem_limit=mem_limit, use_graph=1 if use_graph else 0, autotune=1 if autotune else 0,
-                           spmm_shape=spmm_shape, ema_rows=ema_rows, colors=colors)
+                           spmm_shape=spmm_shape, ema_rows=ema_rows, colors=colors,
+                           unpruned=1 if unpruned else 0)
     est, maps = sgc_count(graph.handle, template.handle, seeds, opt)
     return CountResult(est, maps)
 

@@ -129,7 +129,7 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
                           "/" + std::to_string(bmax) + (o.autotune ? "/tuned" : "") + "/s" +
                           std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows) + "/c" +
-                          std::to_string(o.colors);
+                          std::to_string(o.colors) + (o.unpruned ? "/unpruned" : "");
   for (auto& kv : g->plan_cache)
     if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
       *out = kv.second;
@@ -145,14 +145,16 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     return sh;
   };
   Plan p1;
-  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1, nullptr, o.colors);
+  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1, nullptr, o.colors, o.unpruned != 0);
   if (rc != SGC_OK) return rc;
   if (forced) {
     const std::vector<int> sh = forced_shapes(p1);
-    if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh, o.colors)) != SGC_OK) return rc;
+    if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh,
+                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
   }
   if (p1.ws_bytes > mem_limit)
-    return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) + " bytes of device workspace, limit " +
+    return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) +
+                                 " bytes of device workspace, limit " +
                                  std::to_string(mem_limit));
   const int root = p1.root, policy = p1.policy;
   // Occupancy cap: a SpMM warp keeps a whole output row of `batch` colorings in
@@ -166,11 +168,12 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   set->bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
-    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors);
+    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors, o.unpruned != 0);
     if (rc != SGC_OK) return rc;
     if (forced) {
       const std::vector<int> sh = forced_shapes(pb);
-      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh, o.colors)) != SGC_OK) return rc;
+      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh,
+                          o.colors, o.unpruned != 0)) != SGC_OK) return rc;
     }
     if (pb.ws_bytes > mem_limit) break;
     set->by_batch[b] = std::move(pb);
@@ -272,7 +275,8 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
       for (size_t i = 0; i < nops; ++i)
         if (!cands[i].empty()) shapes[i] = cands[i][std::min(c, cands[i].size() - 1)];
       Plan p;
-      sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes, o.colors);
+      sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes,
+                                o.colors, o.unpruned != 0);
       if (rc != SGC_OK) return rc;
       TimedPass tp;
       if ((rc = time_pass(g, p, pool, st, &tp)) != SGC_OK) return rc;
@@ -312,7 +316,8 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
       report.push_back(te);
     }
     Plan tuned;
-    sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best, o.colors);
+    sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best,
+                              o.colors, o.unpruned != 0);
     if (rc != SGC_OK) return rc;
     set->by_batch[b] = std::move(tuned);
     const double per = pass_ms / b;
@@ -646,6 +651,7 @@ void sgc_options_init(sgc_options* opt) {
   opt->spmm_shape = 0;
   opt->ema_rows = 0;
   opt->colors = 0;
+  opt->unpruned = 0;
 }
 
 const char* sgc_last_error(void) { return g_last_error.c_str(); }
@@ -751,7 +757,8 @@ sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_opt
   if (o.root >= t->k || o.root < -1) return fail(SGC_ERR_INVALID, "options.root out of range");
   Plan p;
   const int b = pow2_floor(std::max(1, std::min(32, o.batch > 0 ? o.batch : 1)));
-  if ((rc = make_plan(g, t, o.precision, o.root, -1, b, false, &p, nullptr, o.colors)) != SGC_OK) return rc;
+  if ((rc = make_plan(g, t, o.precision, o.root, -1, b, false, &p, nullptr,
+                      o.colors, o.unpruned != 0)) != SGC_OK) return rc;
   out->root = p.root;
   out->n_tables = p.n_tables;
   out->n_spmm = p.n_spmm;

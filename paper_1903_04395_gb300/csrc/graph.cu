@@ -148,7 +148,8 @@ __global__ void k_relabel(const int32_t* __restrict__ old_rp, const int32_t* __r
     const int32_t v = blockIdx.x;
     const int32_t o = orig[v];
     const int32_t lo = old_rp[o], deg = old_rp[o + 1] - lo, dst = new_rp[v];
-    for (int32_t j = threadIdx.x; j < deg; j += blockDim.x) relabel_entry(old_ci, n, inv, lo + j, dst + j, new_ci, flags);
+    for (int32_t j = threadIdx.x; j < deg; j += blockDim.x)
+      relabel_entry(old_ci, n, inv, lo + j, dst + j, new_ci, flags);
     return;
   }
   const int lane = threadIdx.x & 31;

@@ -1253,6 +1253,63 @@ __global__ void __launch_bounds__(kBlock) k_final_leaf(const T* __restrict__ P, 
   }
 }
 
+// Ablation of the pruning (Eq. 2, Section 4.2): one combine in Algorithm 1's
+// loop order - for every row, output color set and split the neighbour sum is
+// taken again, instead of once per passive color set (no SpMM).  One thread
+// per (row, output color set).  A single-vertex child's table is all ones and
+// not stored (Ma / Mp null).  npos[c_v][I_p][c_u] is the index of the split's
+// p-set minus c_u in a neighbour's passive row (~0: the neighbour adds nothing).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_unpruned(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_act,
+    const uint8_t* __restrict__ colors, int lb, int k, const T* __restrict__ Ma, int64_t lda,
+    const T* __restrict__ Mp, int64_t ldp, int wp, T* __restrict__ out, int64_t ldt, int ct,
+    const uint2* __restrict__ tab, int nsplit, const uint32_t* __restrict__ npos, int max_deg,
+    const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+  const int batch = 1 << lb;
+  float scale = 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    const float ma = st_a ? state_max(st_a) : 1.f, mp = st_p ? state_max(st_p) : 1.f;
+    s = shift_for((float)nsplit * (float)max_deg * ma * mp);
+    scale = pow2f(-s);
+  }
+  float m = 0.f;
+  const int64_t items = ((int64_t)n_act << lb) * ldt;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = it / ldt;
+    const int S = (int)(it - r * ldt);
+    const int64_t v = r >> lb;
+    const int b = (int)(r & (batch - 1));
+    T acc = T(0);
+    if (S < ct) {
+      const int cv = colors[v * batch + b];
+      const uint32_t* np0 = npos + (int64_t)cv * wp * k;
+      for (int j = 0; j < nsplit; ++j) {
+        const uint2 e = __ldg(tab + (int64_t)j * ct + S);
+        const T a = Ma ? Ma[((v * lda + e.x) << lb) + b] : T(1);
+        if (a == T(0)) continue;
+        const uint32_t* np = np0 + (int64_t)e.y * k;
+        T sum = T(0);
+        for (int32_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q) {
+          const int32_t u = __ldg(col_idx + q);
+          const uint32_t pj = __ldg(np + colors[(int64_t)u * batch + b]);
+          if (pj != 0xFFFFFFFFu) sum += Mp ? Mp[(((int64_t)u * ldp + pj) << lb) + b] : T(1);
+        }
+        acc += a * sum;
+      }
+    }
+    const T val = acc * (T)scale;
+    out[((v * ldt + S) << lb) + b] = val;
+    m = fmaxf(m, (float)val);
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = (st_a ? st_a->e : 0) + (st_p ? st_p->e : 0) + s;
+  }
+}
+
 // More colors than template vertices (Section 2.1, k >= |T|): maps_b = sum_v of
 // all entries of the root table row (every |T|-subset of colors containing
 // c(v)); summed like k_final: the row in the table type, vertices in FP64,
@@ -1373,7 +1430,14 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
   const size_t smem = per_warp * wpb + (size_t)tab_smem * 4;
   if (op.spmm_buckets && op.spmm_variant == 7) {
     const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
-#define SGC_BK(B_)                                                                                             do {                                                                                                           allow_smem(k_spmm_bk<T, B_>, smem);                                                                          k_spmm_bk<T, B_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                                       g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,         colors, k, op.p, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab,         tab_smem, si, so);                                                                                     } while (0)
+#define SGC_BK(B_)                                                                                           \
+  do {                                                                                                       \
+    allow_smem(k_spmm_bk<T, B_>, smem);                                                                      \
+    k_spmm_bk<T, B_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                               \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
+        colors, k, op.p, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.cols_out, (int)op.ld_out, scratch, tab, \
+        tab_smem, si, so);                                                                                   \
+  } while (0)
     switch (batch) {
       case 1: SGC_BK(1); break;
       case 2: SGC_BK(2); break;
@@ -1461,7 +1525,13 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
       while (wr > 1 && per_warp_ring * wr > smem_cap) wr /= 2;
       if (per_warp_ring * wr > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "SpMM ring does not fit in shared memory");
       const size_t smem_r = per_warp_ring * wr;
-#define SGC_RING(R_)                                                                                           do {                                                                                                           allow_smem(k_spmm_ring<T, R_>, smem_r);                                                                      k_spmm_ring<T, R_><<<grid_for(nitems, wr, 1 << 30), 32 * wr, smem_r, st>>>(                                     g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);         } while (0)
+#define SGC_RING(R_)                                                                                         \
+  do {                                                                                                       \
+    allow_smem(k_spmm_ring<T, R_>, smem_r);                                                                  \
+    k_spmm_ring<T, R_><<<grid_for(nitems, wr, 1 << 30), 32 * wr, smem_r, st>>>(                             \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, \
+        colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);       \
+  } while (0)
       if (R == 2) SGC_RING(2);
       else SGC_RING(4);
 #undef SGC_RING
@@ -1663,6 +1733,18 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
         nk += 2;
         break;
+      case OP_UNPRUNED: {
+        const int64_t items = rows * op.ld_out;
+        k_unpruned<T><<<grid_for(items, kBlock, 64 * num_sms), kBlock, 0, st>>>(
+            g->d_row_ptr, g->d_col_idx, g->n_act, colors, lb, plan.k,
+            op.in_a >= 0 ? reinterpret_cast<const T*>(buf(op.in_a)) : nullptr, op.ld_a,
+            op.in_p >= 0 ? reinterpret_cast<const T*>(buf(op.in_p)) : nullptr, op.ld_p, (int)op.cols_p,
+            reinterpret_cast<T*>(buf(op.out)), op.ld_out, (int)op.cols_out,
+            reinterpret_cast<const uint2*>(d_tabs + op.tab_off), (int)op.nsplit, d_tabs + op.tab2_off, g->max_deg,
+            S(op.state_a), S(op.state_p), S(op.state_out));
+        ++nk;
+        break;
+      }
       case OP_FINAL_SUM:
         k_final_rows<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
                                                               (int)op.cols_p, rows, lb, partials);

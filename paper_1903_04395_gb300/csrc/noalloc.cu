@@ -92,7 +92,7 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
   const int want = std::min(32, o.batch > 0 ? o.batch : (int)n_iter);
   while (bmax * 2 <= want) bmax *= 2;
   Plan top;
-  rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &top, nullptr, o.colors);
+  rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &top, nullptr, o.colors, o.unpruned != 0);
   if (rc != SGC_OK) return rc;
   if (static_need(top) > (int64_t)kStaticWorkspaceBytes)
     return fail(SGC_ERR_UNSUPPORTED, "this count needs " + std::to_string(static_need(top)) +
@@ -103,7 +103,8 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
   int bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
-    if ((rc = make_plan(g, t, o.precision, root, policy, b, false, &pb, nullptr, o.colors)) != SGC_OK) return rc;
+    if ((rc = make_plan(g, t, o.precision, root, policy, b, false, &pb, nullptr,
+                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
     if (round_up(pb.ws_bytes, 256) + tab_bytes > (int64_t)kStaticWorkspaceBytes) break;
     bfit = b;
   }
@@ -111,7 +112,8 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
     int b = bfit;
     while (b > n_iter - i) b /= 2;
     Plan plan;
-    if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &plan, nullptr, o.colors)) != SGC_OK) return rc;
+    if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &plan, nullptr,
+                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
     if (static_need(plan) > (int64_t)kStaticWorkspaceBytes)
       return fail(SGC_ERR_INTERNAL, "static workspace plan grew beyond its size");
     char* ws = base;

@@ -314,6 +314,30 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
           h[(size_t)(((int64_t)(cv * k + cu) * L + jl) * nsp + q)] = (uint16_t)pos;
         }
     for (size_t i = 0; i < h.size(); i += 2) tabs->push_back((uint32_t)h[i] | (uint32_t)h[i + 1] << 16);
+  } else if (kind == OP_SPMM + 500) {
+    // unpruned combine: [c_v][I_p][c_u] -> the index, in the passive table row of a
+    // neighbour u of color c_u, of the p-set I_p (relative to c_v) minus c_u, or ~0
+    // when c_u is not in the set (that neighbour adds nothing to this split)
+    const int p = t;
+    const uint64_t w = cr.nsets(p);
+    for (int cv = 0; cv < k; ++cv)
+      for (uint64_t ip = 0; ip < w; ++ip) {
+        const uint32_t rel_v = cr.unrank_mask(ip, p);
+        uint32_t abs_set = 0;
+        for (int x = 0; x < K; ++x)
+          if (rel_v >> x & 1u) abs_set |= 1u << (x < cv ? x : x + 1);
+        for (int cu = 0; cu < k; ++cu) {
+          if (!(abs_set >> cu & 1u)) {
+            tabs->push_back(0xFFFFFFFFu);
+            continue;
+          }
+          const uint32_t rest = abs_set & ~(1u << cu);
+          uint32_t rel_u = 0;
+          for (int y = 0; y < k; ++y)
+            if (rest >> y & 1u) rel_u |= 1u << (y < cu ? y : y - 1);
+          tabs->push_back(cr.rank_mask(rel_u));
+        }
+      }
   } else if (kind == OP_SPMM + 300) {
     // the same positions packed into a-byte entries (a = 1 or 2; all ones = nowhere)
     // for a table staged in shared memory: rows [c_v][c_u] of spmm_packed_ld entries
@@ -496,13 +520,88 @@ static int64_t spmm_cols_per_lane(int batch, int64_t cols_p) {
   return (cols_p + lanes_per_col - 1) / lanes_per_col;
 }
 
+// The ablation plan: Algorithm 1's loop order (vertex, color set, split,
+// neighbour) with no hoisted neighbour sums - one OP_UNPRUNED op per combine
+// reading both children's tables (a single-vertex child's all-ones table is
+// implied) - then the root table summed (OP_FINAL_SUM).  Same colors, tables
+// and results as the pruned plan; work |E| C(k,t) C(t,p) per step instead of
+// |E| C(k,p) + |V| C(k,t) C(t,p) (Lemma 1).
+static void plan_unpruned(const sgc_graph* g, const Builder& B, int k, int tk, int batch, bool build_tabs,
+                          Plan* P) {
+  const int K = k - 1;
+  ColorIndex cr(K);
+  const int elem = P->elem;
+  const int64_t rows = P->rows;
+  const double nv = (double)g->n_act, nnz = (double)g->nnz;
+  const double bw = 6.0e12;
+  std::map<TabKey, int64_t> tcache;
+  std::vector<int> table_buf(B.cls.size(), -1), table_state(B.cls.size(), -1);
+  std::vector<int64_t> table_ld(B.cls.size(), 1), table_w(B.cls.size(), 1);
+  int n_states = 0;
+  PlanOp color_op{};
+  color_op.kind = OP_COLOR;
+  color_op.out = P->buf_colors;
+  color_op.alg_bytes = nv * 4 + nv * batch + 8.0 * batch;
+  P->ops.push_back(color_op);
+  int root_cls = -1;
+  for (size_t c = 0; c < B.cls.size(); ++c) {
+    const Cls& C = B.cls[c];
+    if (C.size == tk) root_cls = (int)c;
+    if (C.a < 0) continue;
+    const Cls& A = B.cls[C.a];
+    const Cls& Pc = B.cls[C.p];
+    PlanOp op{};
+    op.kind = OP_UNPRUNED;
+    op.t = C.size;
+    op.a = A.size;
+    op.p = Pc.size;
+    const int idx = (int)P->ops.size();
+    op.in_a = A.a < 0 ? -1 : table_buf[C.a];
+    op.state_a = A.a < 0 ? -1 : table_state[C.a];
+    op.ld_a = table_ld[C.a];
+    op.cols_a = table_w[C.a];
+    op.in_p = Pc.a < 0 ? -1 : table_buf[C.p];
+    op.state_p = Pc.a < 0 ? -1 : table_state[C.p];
+    op.ld_p = table_ld[C.p];
+    op.cols_p = (int64_t)cr.nsets(Pc.size);  // p-sets of the split (relative to c_v)
+    op.cols_out = (int64_t)cr.nsets(C.size - 1);
+    op.ld_out = pad_ld(op.cols_out, elem);
+    op.nsplit = (int64_t)cr.binom[C.size - 1][Pc.size];
+    op.tab_off = build_tabs ? build_table(cr, k, OP_EMA, C.size, A.size, &P->tabs, &tcache, 0, 0) : 0;
+    op.tab2_off = build_tabs ? build_table(cr, k, (OpKind)(OP_SPMM + 500), Pc.size, 0, &P->tabs, &tcache) : 0;
+    op.state_out = table_state[c] = n_states++;
+    op.out = table_buf[c] = add_buf(P, "U" + std::to_string(c), rows * op.ld_out * elem, idx);
+    table_w[c] = op.cols_out;
+    table_ld[c] = op.ld_out;
+    op.alg_bytes = (double)elem * nv * batch * (double)op.cols_out;
+    op.alg_flops = 2.0 * nnz * batch * (double)op.cols_out * (double)op.nsplit;
+    P->est_cost += nnz * (double)op.cols_out * (double)op.nsplit * elem / bw;
+    P->n_ema++;
+    if (op.in_a >= 0) use_buf(P, op.in_a, idx);
+    if (op.in_p >= 0) use_buf(P, op.in_p, idx);
+    P->ops.push_back(op);
+  }
+  PlanOp op{};
+  op.kind = OP_FINAL_SUM;
+  op.t = tk;
+  op.in_p = table_buf[root_cls];
+  op.state_p = table_state[root_cls];
+  op.cols_p = table_w[root_cls];
+  op.ld_p = table_ld[root_cls];
+  op.out = P->buf_partials;
+  op.alg_bytes = (double)elem * nv * batch * (double)op.cols_p;
+  use_buf(P, op.in_p, (int)P->ops.size());
+  P->ops.push_back(op);
+  P->n_states = n_states;
+}
+
 // `colors` = number of colors k >= |T| (0: k = |T|).  Section 2.1 draws colors
 // from k >= |T|; with k > |T| the root table keeps every (|T|-1)-subset of the
 // other colors and the last op sums its entries (OP_FINAL_SUM) instead of
 // evaluating the single full color set.
 static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy,
                      int batch, bool build_tabs, Plan* P, const std::vector<int>* shapes = nullptr,
-                     int colors = 0) {
+                     int colors = 0, bool unpruned = false) {
   Rooted R;
   root_tree(t, root, &R);
   Builder B(R, policy);
@@ -538,6 +637,21 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   P->final_blocks = (4 * std::max(1, g->num_sms) + 31) / 32 * 32;  // multiple of 32: see k_final
   P->buf_partials = add_buf(P, "partials", 8LL * batch * P->final_blocks, 0);
 
+  if (unpruned) {
+    plan_unpruned(g, B, k, tk, batch, build_tabs, P);
+    P->buf_states = add_buf(P, "states", 8LL * std::max(1, P->n_states), 0);
+    P->scratch_width = 0;
+    P->buf_scratch = add_buf(P, "spmm_scratch", 16, 0);
+    P->buf_hist_heavy = add_buf(P, "hist_heavy", 16, 0);
+    const int last = (int)P->ops.size() - 1;
+    for (int b : {P->buf_seeds, P->buf_colors, P->buf_out, P->buf_partials, P->buf_states, P->buf_scratch,
+                  P->buf_hist_heavy}) {
+      P->bufs[b].first = 0;
+      P->bufs[b].last = last;
+    }
+    place_buffers(P);
+    return;
+  }
   std::vector<int> table_buf(B.cls.size(), -1), pbuf(B.cls.size(), -1);
   std::vector<int> table_state(B.cls.size(), -1), p_state(B.cls.size(), -1);
   std::vector<int64_t> table_w(B.cls.size(), 0), table_ld(B.cls.size(), 0);
@@ -641,7 +755,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.tab_off = !build_tabs             ? 0
                      : op.spmm_variant == 6  ? build_table(cr, k, (OpKind)(OP_SPMM + 400), Pc.size, 32 / batch,
                                                            &P->tabs, &tcache)
-                     : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs, &tcache)
+                     : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs,
+                                                           &tcache)
                      : op.spmm_pos_bytes   ? build_table(cr, k, (OpKind)(OP_SPMM + 300), Pc.size, op.spmm_pos_bytes,
                                                          &P->tabs, &tcache)
                                            : build_table(cr, k, OP_SPMM, Pc.size, 0, &P->tabs, &tcache);
@@ -811,6 +926,17 @@ static bool tables_in_range(const Plan& P, int k) {
       if (n > left) return false;
       for (int64_t i = 0; i < n; ++i)
         if ((int)(t[i] & 0xffu) >= k || (int64_t)(t[i] >> 8) >= op.cols_p) return false;
+    } else if (op.kind == OP_UNPRUNED) {
+      const int64_t n = 2 * op.cols_out * op.nsplit;
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; i += 2)
+        if (t[i] >= (uint32_t)op.cols_a || t[i + 1] >= (uint32_t)op.cols_p) return false;
+      const int64_t n2 = (int64_t)k * op.cols_p * k;
+      if (op.tab2_off < 0 || n2 > (int64_t)P.tabs.size() - op.tab2_off) return false;
+      const uint32_t* t2 = P.tabs.data() + op.tab2_off;
+      const int64_t wpt = op.in_p < 0 ? 1 : op.ld_p;  // entries of a passive row
+      for (int64_t i = 0; i < n2; ++i)
+        if (t2[i] != 0xFFFFFFFFu && (int64_t)t2[i] >= wpt) return false;
     } else if (op.kind == OP_EMA && op.ema_vrpl > 0) {
       const int64_t n = 2 * op.cols_out * op.nsplit;
       if (n > left) return false;
@@ -864,7 +990,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
 }
 
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out, const std::vector<int>* shapes, int colors) {
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes, int colors, bool unpruned) {
   if (colors != 0 && (colors < t->k || colors > SGC_MAX_K))
     return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   if (root >= t->k) return fail(SGC_ERR_INVALID, "options.root is not a template vertex");
@@ -876,7 +1002,7 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
     for (int pol = 0; pol < 2; ++pol) {
       if (policy >= 0 && pol != policy) continue;
       Plan P;
-      plan_for(g, t, precision, r, pol, 1, false, &P, nullptr, colors);
+      plan_for(g, t, precision, r, pol, 1, false, &P, nullptr, colors, unpruned);
       if (best_root < 0 || P.est_cost < best_cost * 0.999 ||
           (P.est_cost <= best_cost * 1.001 && P.ws_bytes < best_ws)) {
         best_root = r;
@@ -886,7 +1012,7 @@ sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, i
       }
     }
   }
-  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out, shapes, colors);
+  plan_for(g, t, precision, best_root, best_policy, batch, build_tabs, out, shapes, colors, unpruned);
   if (build_tabs && !tables_in_range(*out, out->k)) return fail(SGC_ERR_INTERNAL, "index table out of range");
   return SGC_OK;
 }

@@ -129,7 +129,10 @@ enum OpKind : int32_t {
   OP_EMA = 4,        // eMA over the split table (a single-vertex active child needs none)
   OP_FINAL_LEAF = 5, // last step, single-vertex active child, fused with the vertex sum
   OP_FINAL = 6,      // last step, general, fused with the vertex sum
-  OP_FINAL_SUM = 7,  // more colors than template vertices: sum of the root table's entries
+  OP_FINAL_SUM = 7,  // root table summed over all its color sets (more colors than template
+                     // vertices, or after an unpruned combine)
+  OP_UNPRUNED = 8,   // ablation: a combine in Algorithm 1's order, the neighbour sum taken again
+                     // for every color set and split (no SpMM)
 };
 
 struct PlanBuffer {
@@ -167,6 +170,7 @@ struct PlanOp {
   bool ema_sym = false;      // eMA of a table with itself (same buffer, |A| - 1 == |T_p|): each
                              // unordered split once, doubled
   int64_t tab_off = -1;      // offset (uint32 words) of this op's index table
+  int64_t tab2_off = -1;     // OP_UNPRUNED: the neighbour position table
   int state_out = -1, state_a = -1, state_p = -1;  // scale-state slots (FP32)
   double alg_bytes = 0;      // algorithmic HBM bytes of one pass (tables read / written once)
   double alg_flops = 0;      // multiply + add count of one pass
@@ -225,8 +229,10 @@ inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4
 // are only built when build_tabs is set.  `shapes`, when given, holds one
 // launch-shape code per op index (0 = default); codes that do not fit the
 // op (shared memory, form) are ignored.  colors = number of colors (0: |T|).
+// unpruned: the ablation plan of Algorithm 1's loop order (OP_UNPRUNED ops).
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr, int colors = 0);
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr, int colors = 0,
+                     bool unpruned = false);
 
 // The launch shapes worth timing for op `i` of plan p (empty: nothing to choose).
 std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& p, int i);
