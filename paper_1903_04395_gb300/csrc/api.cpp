@@ -2,7 +2,10 @@
 // and the host-side driver of sgc_count (batching colorings, workspace,
 // result read-back and the k^k/k! estimator of Section 2.1).
 #include <algorithm>
+#include <chrono>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -10,9 +13,31 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sgc_internal.h"
 
 namespace sgc {
+
+static bool trace_enabled() {
+  static const bool on = std::getenv("SGC_TRACE") != nullptr;
+  return on;
+}
+
+static long long now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+TraceScope::TraceScope(const char* n) : name(n), t0_ns(0), on(trace_enabled()) {
+  nvtxRangePushA(n);
+  if (on) t0_ns = now_ns();
+}
+
+TraceScope::~TraceScope() {
+  nvtxRangePop();
+  if (on) std::fprintf(stderr, "[sgc] %-16s %9.3f ms\n", name, 1e-6 * (double)(now_ns() - t0_ns));
+}
 
 static thread_local std::string g_last_error;
 
@@ -250,6 +275,7 @@ sgc_status time_pass(const sgc_graph* g, const Plan& plan, DevicePool& pool, cud
 
 sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_options& o, PlanSet* set,
                       DevicePool& pool, cudaStream_t st) {
+  SGC_TRACE_SCOPE("autotune");
   // the largest batch and up to two halvings: wide rows favour smaller batches
   std::vector<int> batches{set->bfit};
   for (int b = set->bfit / 2; b >= 1 && batches.size() < 3 && set->by_batch.count(b); b /= 2) batches.push_back(b);
@@ -416,6 +442,7 @@ sgc_status launch_recorded(const sgc_graph* g, const std::string& key, const std
       g->kernel_launches += x.kernels;
       return SGC_OK;
     }
+  SGC_TRACE_SCOPE("count.record");
   int64_t nk = 0;
   SGC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   sgc_status rc = enqueue_jobs(g, jobs, n_lanes, lane_off, ws, d_seeds, d_maps, n_iter, st, nullptr, &nk);
@@ -506,6 +533,7 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
         (o.mem_limit > 0 ? o.mem_limit : (int64_t)((free_b + pool.bytes) * 0.9)) - staging;
     if (mem_limit <= 0) return fail(SGC_ERR_OOM, "no device memory left for the workspace");
     const int bmax = pow2_floor(std::min(32, o.batch > 0 ? o.batch : std::max(1, (int)n_iter)));
+    SGC_TRACE_SCOPE("count.plan");
     for (int32_t j = 0; j < n_t; ++j) {
       if (ts[j]->k == 1 || g->n_act == 0) continue;
       Job J;
@@ -619,7 +647,10 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
     SGC_CUDA_TRY(cudaGetLastError());
     return SGC_OK;
   }
-  SGC_CUDA_TRY(cudaStreamSynchronize(st));
+  {
+    SGC_TRACE_SCOPE("count.wait");
+    SGC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   SGC_CUDA_TRY(cudaGetLastError());
   if (maps_out) std::memcpy(maps_out, host_maps.data(), sizeof(double) * total);
   if (estimates)

@@ -12,6 +12,9 @@
 #include <cstdlib>
 #include <vector>
 
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
 #include "sgc_internal.h"
 
 namespace sgc {
@@ -210,6 +213,25 @@ sgc_status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return SGC_OK;
 }
 
+// key[v] = maxd - degree (highest degree first; degree 0 last), vid[v] = v
+__global__ void k_degree_keys(const int32_t* __restrict__ rp, int32_t n, int32_t maxd, uint32_t* __restrict__ key,
+                              int32_t* __restrict__ vid) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    key[v] = (uint32_t)(maxd - (rp[v + 1] - rp[v]));
+    vid[v] = (int32_t)v;
+  }
+}
+
+// for the first n_act sorted vertices: inv[orig[i]] = i and deg[i] = maxd - key[i]
+__global__ void k_order_maps(const int32_t* __restrict__ orig, const uint32_t* __restrict__ key_sorted, int32_t n_act,
+                             int32_t maxd, int32_t* __restrict__ inv, int32_t* __restrict__ deg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_act;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    inv[orig[i]] = (int32_t)i;
+    deg[i] = maxd - (int32_t)key_sorted[i];
+  }
+}
+
 // Build the handle from device CSR (d_rp, d_ci) and the host copy of row_ptr.
 sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_t* d_ci,
                        const std::vector<int32_t>& h_rp, uint32_t flags, cudaStream_t st, sgc_graph* g) {
@@ -227,6 +249,7 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
   for (int32_t v = 0; v < n; ++v)
     if (h_rp[v + 1] < h_rp[v]) return fail(SGC_ERR_INVALID, "row_ptr must be non-decreasing");
   if (flags & SGC_GRAPH_VALIDATE) {
+    SGC_TRACE_SCOPE("graph.validate");
     if (nnz % 2 != 0) return fail(SGC_ERR_INVALID, "an undirected simple graph has an even nnz");
     // flags word, then the searched / skipped entry counts of the symmetry check
     int32_t* d_flags = nullptr;
@@ -270,61 +293,107 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
       return fail(SGC_ERR_INVALID, "invalid CSR:" + why);
     }
   }
-  // degree order, highest first, ties by original id; degree-0 vertices dropped
-  int32_t maxd = 0;
-  for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, h_rp[v + 1] - h_rp[v]);
-  std::vector<int64_t> bucket((size_t)maxd + 2, 0);
-  for (int32_t v = 0; v < n; ++v) bucket[(size_t)(maxd - (h_rp[v + 1] - h_rp[v]))]++;
-  int64_t run = 0;
-  for (auto& b : bucket) { int64_t c = b; b = run; run += c; }
-  std::vector<int32_t> order((size_t)n), inv((size_t)n, -1);
-  for (int32_t v = 0; v < n; ++v) order[(size_t)bucket[(size_t)(maxd - (h_rp[v + 1] - h_rp[v]))]++] = v;
-  int32_t n_act = 0;
-  while (n_act < n && h_rp[order[n_act] + 1] - h_rp[order[n_act]] > 0) ++n_act;
-  order.resize((size_t)n_act);
-  for (int32_t i = 0; i < n_act; ++i) inv[(size_t)order[i]] = i;
-  std::vector<int32_t> new_rp((size_t)n_act + 1, 0);
-  g->h_degree_sorted.resize((size_t)n_act);
-  for (int32_t i = 0; i < n_act; ++i) {
-    const int32_t d = h_rp[order[i] + 1] - h_rp[order[i]];
-    g->h_degree_sorted[(size_t)i] = d;
-    new_rp[(size_t)i + 1] = new_rp[(size_t)i] + d;
+  // degree order, highest first, ties by original id; degree-0 vertices dropped.
+  // On the device: key = maxd - degree, a stable radix sort of (key, vertex)
+  // pairs (ties keep id order), then the inverse map, the sorted degrees and
+  // the new row_ptr by an exclusive scan.  The host only needs the degrees of
+  // the heavy prefix (for the segments) and of the wide prefix (relabelling).
+  SGC_TRACE_SCOPE("graph.order");
+  int32_t maxd = 0, n_iso = 0, n_heavy_h = 0, n_wide_h = 0;
+  g->seg_len = default_seg_len();
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = h_rp[v + 1] - h_rp[v];
+    maxd = std::max(maxd, d);
+    n_iso += d == 0;
+    n_heavy_h += d > g->seg_len;
+    n_wide_h += d > kWideRow;
   }
+  const int32_t n_act = n - n_iso;
   g->n_act = n_act;
   g->max_deg = maxd;
-  g->seg_len = default_seg_len();
+  int key_bits = 1;
+  while (key_bits < 31 && ((int64_t)1 << key_bits) <= maxd) ++key_bits;
+  // device buffers: keys in/out, vertices in/out (the sorted vertices become d_orig)
+  uint32_t *d_key = nullptr, *d_key_s = nullptr;
+  int32_t *d_vid = nullptr, *d_inv = nullptr, *d_flags = nullptr;
+  void* d_tmp = nullptr;
+  size_t tmp_sort = 0, tmp_scan = 0;
+  cudaError_t e = cudaSuccess;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, 65536));
+  auto dev_fail = [&](cudaError_t err, const char* what) {
+    cudaFree(d_key);
+    cudaFree(d_key_s);
+    cudaFree(d_vid);
+    cudaFree(d_inv);
+    cudaFree(d_flags);
+    cudaFree(d_tmp);
+    return cuda_fail(err, what);
+  };
+  if (n > 0) {
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_sort, d_key, d_key_s, d_vid, g->d_orig, n, 0, key_bits, st);
+    cub::DeviceScan::ExclusiveSum(nullptr, tmp_scan, (const int32_t*)nullptr, (int32_t*)nullptr, n_act + 1, st);
+  }
+  const size_t tmp_bytes = std::max<size_t>({tmp_sort, tmp_scan, 16});
+  if ((e = cudaMalloc(&d_key, sizeof(uint32_t) * std::max(n, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&d_key_s, sizeof(uint32_t) * std::max(n, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&d_vid, sizeof(int32_t) * ((size_t)std::max(n, 1) + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_orig, sizeof(int32_t) * std::max(n, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&d_inv, sizeof(int32_t) * std::max(n, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * ((size_t)n_act + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&d_tmp, tmp_bytes)) != cudaSuccess)
+    return dev_fail(e, "cudaMalloc(graph order)");
+  if (n > 0) {
+    k_degree_keys<<<nb, 256, 0, st>>>(d_rp, n, maxd, d_key, d_vid);
+    e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_sort, d_key, d_key_s, d_vid, g->d_orig, n, 0, key_bits, st);
+    if (e != cudaSuccess) return dev_fail(e, "sorting the vertices by degree");
+    // d_vid now takes the sorted degrees (n_act of them, then a 0 for the scan's total)
+    if ((e = cudaMemsetAsync(d_inv, 0xFF, sizeof(int32_t) * n, st)) != cudaSuccess)
+      return dev_fail(e, "graph order");
+    k_order_maps<<<nb, 256, 0, st>>>(g->d_orig, d_key_s, n_act, maxd, d_inv, d_vid);
+    if ((e = cudaMemsetAsync(d_vid + n_act, 0, sizeof(int32_t), st)) != cudaSuccess) return dev_fail(e, "graph order");
+    e = cub::DeviceScan::ExclusiveSum(d_tmp, tmp_scan, d_vid, g->d_row_ptr, n_act + 1, st);
+    if (e != cudaSuccess) return dev_fail(e, "row_ptr scan");
+  } else {
+    if ((e = cudaMemsetAsync(g->d_row_ptr, 0, sizeof(int32_t), st)) != cudaSuccess) return dev_fail(e, "graph order");
+  }
+  // the heavy prefix's degrees and row starts, for the segments
+  const int32_t n_pref = std::max(n_heavy_h, std::min(n_wide_h, 65536));
+  std::vector<int32_t> pref_deg((size_t)n_pref), pref_rp((size_t)n_pref + 1);
+  if (n_pref > 0) {
+    if ((e = cudaMemcpyAsync(pref_deg.data(), d_vid, sizeof(int32_t) * n_pref, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(pref_rp.data(), g->d_row_ptr, sizeof(int32_t) * ((size_t)n_pref + 1),
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return dev_fail(e, "reading the heavy rows");
+  }
   // heavy rows are a prefix; cut their neighbour lists into seg_len pieces
   std::vector<int32_t> seg_row, seg_lo, seg_hi, heavy_seg(1, 0);
-  int32_t n_heavy = 0;
-  while (n_heavy < n_act && g->h_degree_sorted[(size_t)n_heavy] > g->seg_len) {
-    const int32_t lo = new_rp[(size_t)n_heavy], hi = new_rp[(size_t)n_heavy + 1];
+  const int32_t n_heavy = n_heavy_h;
+  for (int32_t r = 0; r < n_heavy; ++r) {
+    const int32_t lo = pref_rp[(size_t)r], hi = pref_rp[(size_t)r + 1];
     for (int32_t s = lo; s < hi; s += g->seg_len) {
-      seg_row.push_back(n_heavy);
+      seg_row.push_back(r);
       seg_lo.push_back(s);
       seg_hi.push_back(std::min(hi, s + g->seg_len));
     }
     heavy_seg.push_back((int32_t)seg_row.size());
-    ++n_heavy;
   }
   g->n_heavy = n_heavy;
   g->n_seg = (int32_t)seg_row.size();
   sgc_status rc;
-  if ((rc = upload(&g->d_row_ptr, new_rp, st)) != SGC_OK) return rc;
-  if ((rc = upload(&g->d_orig, order, st)) != SGC_OK) return rc;
-  if ((rc = upload(&g->d_seg_row, seg_row, st)) != SGC_OK) return rc;
-  if ((rc = upload(&g->d_seg_lo, seg_lo, st)) != SGC_OK) return rc;
-  if ((rc = upload(&g->d_seg_hi, seg_hi, st)) != SGC_OK) return rc;
-  if ((rc = upload(&g->d_heavy_seg, heavy_seg, st)) != SGC_OK) return rc;
-  int32_t* d_inv = nullptr;
-  if ((rc = upload(&d_inv, inv, st)) != SGC_OK) return rc;
-  int32_t* d_flags = nullptr;
+  if ((rc = upload(&g->d_seg_row, seg_row, st)) != SGC_OK || (rc = upload(&g->d_seg_lo, seg_lo, st)) != SGC_OK ||
+      (rc = upload(&g->d_seg_hi, seg_hi, st)) != SGC_OK || (rc = upload(&g->d_heavy_seg, heavy_seg, st)) != SGC_OK) {
+    dev_fail(cudaSuccess, "");
+    return rc;
+  }
+  SGC_TRACE_SCOPE("graph.relabel");  // waits for the CSR copy to the device too
   int32_t h_flags = 0;
-  cudaError_t e = cudaMalloc(&g->d_col_idx, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+  e = cudaMalloc(&g->d_col_idx, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&d_flags, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), st);
   if (e == cudaSuccess && n_act > 0) {
-    int32_t n_wide = 0;  // rows in degree order: the long ones are a prefix
-    while (n_wide < n_act && n_wide < 65536 && g->h_degree_sorted[(size_t)n_wide] > kWideRow) ++n_wide;
+    const int32_t n_wide = std::min(n_wide_h, 65536);  // rows in degree order: the long ones are a prefix
     const int64_t light_blocks = std::min<int64_t>((n_act - n_wide + 7) / 8, 65536);
     k_relabel<<<n_wide + std::max<int64_t>(light_blocks, 1), 256, 0, st>>>(
         d_rp, d_ci, n, g->d_orig, d_inv, g->d_row_ptr, n_act, n_wide, g->d_col_idx, d_flags);
@@ -332,7 +401,11 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_key);
+  cudaFree(d_key_s);
+  cudaFree(d_vid);
   cudaFree(d_inv);
+  cudaFree(d_tmp);
   if (d_flags) cudaFree(d_flags);
   if (e != cudaSuccess) return cuda_fail(e, "graph relabel");
   if (h_flags & BAD_COL) return fail(SGC_ERR_INVALID, "invalid CSR: column index out of range");
@@ -346,6 +419,7 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
 // the host-side ordering, then build.  The raw copy is released either way.
 sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, bool on_device,
                              uint32_t flags, cudaStream_t user_stream, sgc_graph** out) {
+  SGC_TRACE_SCOPE("graph.create");
   if (!out) return fail(SGC_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (n < 0 || nnz < 0 || nnz > INT32_MAX) return fail(SGC_ERR_INVALID, "n and nnz must be in [0, 2^31)");

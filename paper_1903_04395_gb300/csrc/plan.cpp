@@ -702,6 +702,12 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.state_p = table_state[C.p];
         op.spmm_buckets = spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketMaxBytes;
         op.spmm_variant = op.spmm_buckets ? 7 : default_spmm_variant();
+        if (op.spmm_buckets && batch >= 8 && op.ld_out < 65535) {
+          // narrow rows at 8+ colorings per pass: the direct form with the lane-major table
+          // measured faster than the buckets (R-MAT 20 spider, p = 2: 3.4 vs 4.1 ms)
+          op.spmm_buckets = false;
+          op.spmm_variant = 6;
+        }
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
         if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
           op.spmm_buckets = true;

@@ -27,6 +27,22 @@ sgc_status cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::sgc::cuda_fail(_e, #expr); \
   } while (0)
 
+// ---------------------------------------------------------------- tracing
+// Every traced phase is an NVTX range (visible to ncu --nvtx and Nsight); with
+// SGC_TRACE set in the environment its host wall time also goes to stderr.
+struct TraceScope {
+  const char* name;
+  long long t0_ns;
+  bool on;
+  explicit TraceScope(const char* n);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+};
+#define SGC_CAT2(a, b) a##b
+#define SGC_CAT(a, b) SGC_CAT2(a, b)
+#define SGC_TRACE_SCOPE(name) ::sgc::TraceScope SGC_CAT(sgc_trace_scope_, __LINE__)(name)
+
 // ------------------------------------------------ color-set index (Eq. 1)
 // Columns of a count table for sub-templates of size h are the h-subsets of
 // the k colors, numbered by Eq. 1: I(C) = sum_i binom(c_i, i) with the colors
@@ -102,7 +118,6 @@ struct sgc_graph {
   mutable sgc::Profiler prof;
   mutable int64_t kernel_launches = 0;    // kernels enqueued by calls on this handle
   mutable std::vector<std::pair<std::string, std::shared_ptr<sgc::PlanSet>>> plan_cache;
-  std::vector<int32_t> h_degree_sorted;  // degrees in new numbering (host copy)
   mutable std::vector<cudaStream_t> lanes;       // side streams for templates counted side by side
   mutable std::vector<cudaEvent_t> lane_events;  // fork (0) and join (1..) events of those streams
   mutable std::vector<sgc::ExecEntry> exec_cache;
