@@ -76,6 +76,8 @@ def parse():
                     help="R-MAT scale override (small cases for profiling; not a bench configuration)")
     ap.add_argument("--batch", type=int, default=None, help="colorings per pass override")
     ap.add_argument("--spmm-shape", type=int, default=0, help="force an SpMM launch shape (sgc_options.spmm_shape)")
+    ap.add_argument("--rcm", action="store_true",
+                    help="number the graph's rows in reverse Cuthill-McKee order (SGC_GRAPH_ORDER_RCM)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.scale is not None:
@@ -652,7 +654,7 @@ def main():
     torch.cuda.set_stream(stream)
     d_rp = torch.from_numpy(rp).cuda()
     d_ci = torch.from_numpy(ci).cuda()
-    g = sgc.Graph.from_device(n, nnz, d_rp.data_ptr(), d_ci.data_ptr(), stream=stream.cuda_stream)
+    g = sgc.Graph.from_device(n, nnz, d_rp.data_ptr(), d_ci.data_ptr(), stream=stream.cuda_stream, rcm=args.rcm)
     templates = [(name, sgc.Template(make_parent(spec))) for name, spec in wl["templates"]]
     NT = len(templates)
     K, W = args.steps, args.warmup
@@ -717,6 +719,7 @@ def main():
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": config_of(wl, world)}
     res["config"]["autotune"] = bool(tune)
+    res["config"]["row_order"] = "reverse Cuthill-McKee after the rows longer than 256" if args.rcm else "degree"
     if tune:
         res["tuned_shapes"] = {}
         for name, t in templates:
@@ -778,7 +781,8 @@ def main():
         k_e2e = max(3, K // 6)
 
         def e2e_step(s):
-            gh = sgc.sgc_graph_create(n, nnz, h_rp.data_ptr(), h_ci.data_ptr(), sgc.SGC_GRAPH_VALIDATE)
+            gh = sgc.sgc_graph_create(n, nnz, h_rp.data_ptr(), h_ci.data_ptr(),
+                                      sgc.SGC_GRAPH_VALIDATE | (sgc.SGC_GRAPH_ORDER_RCM if args.rcm else 0))
             try:
                 for ti, (_, t) in enumerate(templates):
                     sd = np.arange(B, dtype=np.uint64) + np.uint64(50_000_000 + rank * 1_000_000 + (s * NT + ti) * B)

@@ -61,6 +61,9 @@ typedef struct sgc_template sgc_template;
 
 /* Graph creation flags. */
 #define SGC_GRAPH_VALIDATE 1u   /* check CSR invariants on the device (recommended) */
+#define SGC_GRAPH_ORDER_RCM 2u  /* renumber the rows of degree <= 256 in reverse Cuthill-McKee order
+                                   (Section 4.3's locality pre-processing) instead of by degree;
+                                   computed on the host, O(nnz log d) */
 
 typedef struct sgc_options {
   int32_t precision;   /* sgc_precision; default SGC_FP32 */
@@ -120,7 +123,11 @@ int32_t sgc_version(void);
  *   flags    SGC_GRAPH_VALIDATE checks all of the above (SGC_ERR_INVALID)
  * The library copies the CSR to the device, drops isolated vertices (they
  * are in no embedding of a template with k >= 2) and renumbers the rest by
- * degree, highest first; counts do not depend on vertex numbering.
+ * degree, highest first; with SGC_GRAPH_ORDER_RCM only the rows longer than
+ * 256 stay first by degree and the others follow in reverse Cuthill-McKee
+ * order (neighbouring rows get nearby numbers, so the SpMM's gathers reuse
+ * cached rows).  Counts do not depend on vertex numbering: colors are drawn
+ * from the original ids.
  */
 sgc_status sgc_graph_create(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                             uint32_t flags, sgc_graph** out);
@@ -140,6 +147,7 @@ typedef struct sgc_graph_stats {
   int32_t n_segments; /* neighbour-list segments of those rows */
   int32_t device;     /* CUDA device ordinal */
   int64_t kernel_launches; /* kernels enqueued so far by calls on this handle */
+  int32_t ordering;   /* 0 = rows by degree, 1 = reverse Cuthill-McKee (SGC_GRAPH_ORDER_RCM) */
 } sgc_graph_stats;
 
 sgc_status sgc_graph_stats_get(const sgc_graph* g, sgc_graph_stats* out);

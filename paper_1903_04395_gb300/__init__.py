@@ -23,6 +23,7 @@ SGC_OK, SGC_ERR_INVALID, SGC_ERR_OOM, SGC_ERR_CUDA = 0, 1, 2, 3
 SGC_ERR_TIMEOUT, SGC_ERR_OVERFLOW, SGC_ERR_INTERNAL, SGC_ERR_UNSUPPORTED = 4, 5, 6, 7
 SGC_FP32, SGC_FP64 = 0, 1
 SGC_GRAPH_VALIDATE = 1
+SGC_GRAPH_ORDER_RCM = 2
 SGC_MAX_K = 16
 
 _STATUS = {0: "SGC_OK", 1: "SGC_ERR_INVALID", 2: "SGC_ERR_OOM", 3: "SGC_ERR_CUDA", 4: "SGC_ERR_TIMEOUT",
@@ -45,7 +46,7 @@ class sgc_options(ctypes.Structure):
 class sgc_graph_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_active", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("max_degree", ctypes.c_int32), ("n_heavy", ctypes.c_int32), ("n_segments", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
+                ("device", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("ordering", ctypes.c_int32)]
 
 
 class sgc_plan_info(ctypes.Structure):
@@ -385,16 +386,18 @@ class Server:
 class Graph:
     """Owning wrapper of an sgc_graph handle."""
 
-    def __init__(self, row_ptr, col_idx, validate: bool = True):
+    def __init__(self, row_ptr, col_idx, validate: bool = True, rcm: bool = False):
         row_ptr = np.asarray(row_ptr)
         n = len(row_ptr) - 1
-        self.handle = sgc_graph_create(n, len(col_idx), row_ptr, col_idx, SGC_GRAPH_VALIDATE if validate else 0)
+        flags = (SGC_GRAPH_VALIDATE if validate else 0) | (SGC_GRAPH_ORDER_RCM if rcm else 0)
+        self.handle = sgc_graph_create(n, len(col_idx), row_ptr, col_idx, flags)
 
     @classmethod
-    def from_device(cls, n: int, nnz: int, d_row_ptr: int, d_col_idx: int, validate: bool = True, stream=None):
+    def from_device(cls, n: int, nnz: int, d_row_ptr: int, d_col_idx: int, validate: bool = True, stream=None,
+                    rcm: bool = False):
         self = cls.__new__(cls)
-        self.handle = sgc_graph_create_device(n, nnz, d_row_ptr, d_col_idx,
-                                              SGC_GRAPH_VALIDATE if validate else 0, stream)
+        flags = (SGC_GRAPH_VALIDATE if validate else 0) | (SGC_GRAPH_ORDER_RCM if rcm else 0)
+        self.handle = sgc_graph_create_device(n, nnz, d_row_ptr, d_col_idx, flags, stream)
         return self
 
     def stats(self) -> dict:

@@ -710,6 +710,7 @@ sgc_status sgc_graph_stats_get(const sgc_graph* g, sgc_graph_stats* out) {
   out->device = g->device;
   std::lock_guard<std::mutex> lock(g->mu);
   out->kernel_launches = g->kernel_launches;
+  out->ordering = g->ordering;
   return SGC_OK;
 }
 

@@ -222,19 +222,79 @@ __global__ void k_degree_keys(const int32_t* __restrict__ rp, int32_t n, int32_t
   }
 }
 
-// for the first n_act sorted vertices: inv[orig[i]] = i and deg[i] = maxd - key[i]
-__global__ void k_order_maps(const int32_t* __restrict__ orig, const uint32_t* __restrict__ key_sorted, int32_t n_act,
-                             int32_t maxd, int32_t* __restrict__ inv, int32_t* __restrict__ deg) {
+// for the first n_act vertices of the new order: inv[orig[i]] = i and deg[i] = degree of orig[i]
+__global__ void k_order_maps(const int32_t* __restrict__ orig, const int32_t* __restrict__ rp, int32_t n_act,
+                             int32_t* __restrict__ inv, int32_t* __restrict__ deg) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_act;
        i += (int64_t)gridDim.x * blockDim.x) {
-    inv[orig[i]] = (int32_t)i;
-    deg[i] = maxd - (int32_t)key_sorted[i];
+    const int32_t v = orig[i];
+    inv[v] = (int32_t)i;
+    deg[i] = rp[v + 1] - rp[v];
   }
+}
+
+// Reverse Cuthill-McKee order of the rows of degree 1..thr (Section 4.3 names
+// RCM as the locality pre-processing of the adjacency matrix), after the rows
+// of degree > thr in degree order (highest first, ties by id) and before the
+// isolated vertices (by id).  Breadth-first search over the light rows only:
+// each component starts at its unvisited row of lowest degree (ties by id),
+// a row's unvisited light neighbours are queued by increasing degree (ties by
+// id), and the whole light sequence is then reversed.  Neighbours of the
+// heavy rows are not expanded through them, so a hub does not pull its
+// thousands of otherwise unrelated neighbours together.  Column indices
+// outside [0, n) are skipped here (validation or relabelling reports them).
+void rcm_order(int32_t n, const std::vector<int32_t>& rp, const int32_t* ci, int32_t thr,
+               std::vector<int32_t>* orig) {
+  orig->clear();
+  orig->reserve((size_t)n);
+  std::vector<int32_t> deg((size_t)n);
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    deg[(size_t)v] = rp[(size_t)v + 1] - rp[(size_t)v];
+    maxd = std::max(maxd, deg[(size_t)v]);
+  }
+  // counting sort by degree: descending for the heavy prefix, ascending for the start list
+  std::vector<int64_t> cnt((size_t)maxd + 2, 0);
+  for (int32_t v = 0; v < n; ++v) ++cnt[(size_t)deg[(size_t)v] + 1];
+  for (size_t d = 1; d < cnt.size(); ++d) cnt[d] += cnt[d - 1];
+  std::vector<int32_t> by_deg((size_t)n);  // ascending degree, ties by id
+  for (int32_t v = 0; v < n; ++v) by_deg[(size_t)cnt[(size_t)deg[(size_t)v]]++] = v;
+  for (int32_t d = maxd; d > thr; --d) {
+    // the vertices of degree d sit in by_deg[start of d .. end of d) in id order
+    const int64_t hi = cnt[(size_t)d], lo = d > 0 ? cnt[(size_t)d - 1] : 0;
+    for (int64_t i = lo; i < hi; ++i) orig->push_back(by_deg[(size_t)i]);
+  }
+  std::vector<uint8_t> seen((size_t)n, 0);
+  for (int32_t v = 0; v < n; ++v) seen[(size_t)v] = deg[(size_t)v] == 0 || deg[(size_t)v] > thr;
+  const size_t light0 = orig->size();
+  std::vector<std::pair<int32_t, int32_t>> nb;
+  for (int32_t s : by_deg) {
+    if (seen[(size_t)s]) continue;
+    seen[(size_t)s] = 1;
+    size_t head = orig->size();
+    orig->push_back(s);
+    while (head < orig->size()) {
+      const int32_t x = (*orig)[head++];
+      nb.clear();
+      for (int32_t e = rp[(size_t)x]; e < rp[(size_t)x + 1]; ++e) {
+        const int32_t w = ci[e];
+        if (w < 0 || w >= n || seen[(size_t)w]) continue;
+        seen[(size_t)w] = 1;
+        nb.emplace_back(deg[(size_t)w], w);
+      }
+      std::sort(nb.begin(), nb.end());
+      for (const auto& dw : nb) orig->push_back(dw.second);
+    }
+  }
+  std::reverse(orig->begin() + (std::ptrdiff_t)light0, orig->end());
+  for (int32_t v = 0; v < n; ++v)
+    if (deg[(size_t)v] == 0) orig->push_back(v);
 }
 
 // Build the handle from device CSR (d_rp, d_ci) and the host copy of row_ptr.
 sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_t* d_ci,
-                       const std::vector<int32_t>& h_rp, uint32_t flags, cudaStream_t st, sgc_graph* g) {
+                       const std::vector<int32_t>& h_rp, const int32_t* h_ci, uint32_t flags, cudaStream_t st,
+                       sgc_graph* g) {
   int dev = 0, sms = 0;
   SGC_CUDA_TRY(cudaGetDevice(&dev));
   SGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -298,6 +358,8 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
   // pairs (ties keep id order), then the inverse map, the sorted degrees and
   // the new row_ptr by an exclusive scan.  The host only needs the degrees of
   // the heavy prefix (for the segments) and of the wide prefix (relabelling).
+  // SGC_GRAPH_ORDER_RCM: the same prefix of long rows, the rest in reverse
+  // Cuthill-McKee order, computed on the host (rcm_order) and uploaded.
   SGC_TRACE_SCOPE("graph.order");
   int32_t maxd = 0, n_iso = 0, n_heavy_h = 0, n_wide_h = 0;
   g->seg_len = default_seg_len();
@@ -342,14 +404,33 @@ sgc_status build_graph(int32_t n, int64_t nnz, const int32_t* d_rp, const int32_
       (e = cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * ((size_t)n_act + 1))) != cudaSuccess ||
       (e = cudaMalloc(&d_tmp, tmp_bytes)) != cudaSuccess)
     return dev_fail(e, "cudaMalloc(graph order)");
-  if (n > 0) {
+  if (n > 0 && (flags & SGC_GRAPH_ORDER_RCM)) {
+    std::vector<int32_t> h_ci_copy;
+    if (!h_ci && nnz > 0) {
+      h_ci_copy.resize((size_t)nnz);
+      if ((e = cudaMemcpyAsync(h_ci_copy.data(), d_ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost,
+                               st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return dev_fail(e, "reading col_idx for the RCM order");
+      h_ci = h_ci_copy.data();
+    }
+    std::vector<int32_t> order;
+    rcm_order(n, h_rp, h_ci, std::min(g->seg_len, kWideRow), &order);
+    if ((e = cudaMemcpyAsync(g->d_orig, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)  // `order` is released on return
+      return dev_fail(e, "uploading the RCM order");
+    g->ordering = 1;
+  } else if (n > 0) {
     k_degree_keys<<<nb, 256, 0, st>>>(d_rp, n, maxd, d_key, d_vid);
     e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_sort, d_key, d_key_s, d_vid, g->d_orig, n, 0, key_bits, st);
     if (e != cudaSuccess) return dev_fail(e, "sorting the vertices by degree");
-    // d_vid now takes the sorted degrees (n_act of them, then a 0 for the scan's total)
+  }
+  if (n > 0) {
+    // d_vid now takes the degrees in the new order (n_act of them, then a 0 for the scan's total)
     if ((e = cudaMemsetAsync(d_inv, 0xFF, sizeof(int32_t) * n, st)) != cudaSuccess)
       return dev_fail(e, "graph order");
-    k_order_maps<<<nb, 256, 0, st>>>(g->d_orig, d_key_s, n_act, maxd, d_inv, d_vid);
+    k_order_maps<<<nb, 256, 0, st>>>(g->d_orig, d_rp, n_act, d_inv, d_vid);
     if ((e = cudaMemsetAsync(d_vid + n_act, 0, sizeof(int32_t), st)) != cudaSuccess) return dev_fail(e, "graph order");
     e = cub::DeviceScan::ExclusiveSum(d_tmp, tmp_scan, d_vid, g->d_row_ptr, n_act + 1, st);
     if (e != cudaSuccess) return dev_fail(e, "row_ptr scan");
@@ -440,7 +521,7 @@ sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, con
     if (e == cudaSuccess)
       e = cudaMemcpy(h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "reading device row_ptr");
-    if (rc == SGC_OK) rc = build_graph(n, nnz, row_ptr, col_idx, h_rp, flags, st, g);
+    if (rc == SGC_OK) rc = build_graph(n, nnz, row_ptr, col_idx, h_rp, nullptr, flags, st, g);
   } else {
     std::copy(row_ptr, row_ptr + n + 1, h_rp.begin());
     e = cudaMalloc(&d_rp, sizeof(int32_t) * ((size_t)n + 1));
@@ -451,7 +532,7 @@ sgc_status graph_create_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, con
       e = cudaMemcpyAsync(d_ci, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? fail(SGC_ERR_OOM, "device memory for the graph")
                                                               : cuda_fail(e, "uploading the graph");
-    if (rc == SGC_OK) rc = build_graph(n, nnz, d_rp, d_ci, h_rp, flags, st, g);
+    if (rc == SGC_OK) rc = build_graph(n, nnz, d_rp, d_ci, h_rp, col_idx, flags, st, g);
     cudaStreamSynchronize(st);
     if (d_rp) cudaFree(d_rp);
     if (d_ci) cudaFree(d_ci);

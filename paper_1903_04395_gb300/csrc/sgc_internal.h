@@ -100,12 +100,13 @@ struct sgc_graph {
   int num_sms = 0;
   int smem_optin = 0;     // bytes of shared memory a block may opt into
   int32_t n = 0;          // vertices as given
-  int32_t n_act = 0;      // vertices with degree > 0, renumbered by degree (desc)
+  int32_t n_act = 0;      // vertices with degree > 0, renumbered (by degree, desc, or RCM)
   int64_t nnz = 0;
   int32_t max_deg = 0;
   int32_t seg_len = 0;    // neighbour-list segment length for heavy rows
   int32_t n_heavy = 0;    // rows 0..n_heavy-1 have degree > seg_len
   int32_t n_seg = 0;      // segments covering the heavy rows
+  int32_t ordering = 0;   // 0 = rows by degree, 1 = heavy prefix by degree + reverse Cuthill-McKee
   int32_t* d_row_ptr = nullptr;   // n_act + 1
   int32_t* d_col_idx = nullptr;   // nnz, new numbering
   int32_t* d_orig = nullptr;      // n_act: original id of each new vertex
