@@ -91,8 +91,10 @@ typedef struct sgc_options {
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
-                          1 / 2 rows per lane (4..32 colorings per pass); ops it does not fit keep
-                          theirs; 0 (default) = planner or autotuner */
+                          1 / 2 rows per lane (4..32 colorings per pass), or 103 = every operand in
+                          registers (FP32; the shapes compiled in: 10 colors with a 3-color passive
+                          child and a 3-color active one, the default where it applies); ops it
+                          does not fit keep theirs; 0 (default) = planner or autotuner */
   int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
                           |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have
                           distinct colors; the estimate divides by k! / ((k - |T|)! k^|T|). */

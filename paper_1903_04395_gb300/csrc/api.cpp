@@ -498,8 +498,8 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
     return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..13");
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != 2 && o.ema_rows != 1 && o.ema_rows != kShapeEmaVertex1 &&
-      o.ema_rows != kShapeEmaVertex2)
-    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101 or 102");
+      o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg)
+    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101, 102 or 103");
   SGC_CUDA_TRY(cudaSetDevice(g->device));
   std::lock_guard<std::mutex> lock(g->mu);
   DevicePool& pool = device_pool(g->device);

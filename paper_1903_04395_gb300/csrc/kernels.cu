@@ -34,6 +34,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <type_traits>
+#include <utility>
 
 #include "sgc_internal.h"
 
@@ -1197,6 +1198,141 @@ __global__ void __launch_bounds__(kBlock) k_ema_v(
   }
 }
 
+// eMA with every operand in registers, for a few (K, a-1, p) shapes compiled
+// in: one thread per (vertex, coloring) row holds the passive row P(v, .)
+// and the output row in registers and streams the active row: for each
+// (a-1)-subset A of the K relative colors, M_a(v, A) is loaded (or, in the
+// symmetric form, taken from the registers) once and multiplied into every
+// output S = A + S_p over the p-subsets S_p of the other colors.  The splits
+// are fixed by the subset sizes alone (both rows are relative to the same
+// color c(v)), so their index pairs are constants generated at compile time
+// and the FMAs address registers directly: no table, no shared memory, and
+// the kernel streams the three tables once (HBM-bound instead of bound by
+// shared-memory operand reads).  The A subsets are visited in decreasing
+// mask order, the order in which the split table lists the splits of every
+// S, so each output receives its terms in the same order as k_ema / k_ema_v:
+// the FP32 sums are the same.
+__host__ __device__ constexpr int c_binom(int n, int r) {
+  if (r < 0 || r > n) return 0;
+  int64_t x = 1;
+  for (int i = 1; i <= r; ++i) x = x * (n - r + i) / i;
+  return (int)x;
+}
+__host__ __device__ constexpr int c_popc(uint32_t m) {
+  int c = 0;
+  for (; m; m >>= 1) c += (int)(m & 1u);
+  return c;
+}
+// Eq. 1: colex rank of the set of ascending colors c_1 < c_2 < ..: sum_i C(c_i, i)
+__host__ __device__ constexpr int c_rank(uint32_t m) {
+  int r = 0, i = 0;
+  for (int c = 0; c < 32; ++c)
+    if (m >> c & 1u) r += c_binom(c, ++i);
+  return r;
+}
+
+template <int K, int AR, int PR, bool SYM>
+struct EmaRegPlan {
+  static constexpr int NA = c_binom(K, AR), NP = c_binom(K, PR), NO = c_binom(K, AR + PR);
+  static constexpr int NPAIR = NO * (SYM ? c_binom(AR + PR, AR) / 2 : c_binom(AR + PR, AR));
+  struct Tab {
+    int16_t ga[NA];         // A index of group g (groups in decreasing mask order)
+    int16_t g0[NA + 1];     // first pair of group g
+    int16_t p[NPAIR], o[NPAIR];
+  };
+  static constexpr Tab make() {
+    Tab t{};
+    int n = 0, g = 0;
+    for (uint32_t m = 1u << K; m-- > 0;) {
+      if (c_popc(m) != AR) continue;
+      const uint32_t rest = ((1u << K) - 1) & ~m;
+      t.ga[g] = (int16_t)c_rank(m);
+      t.g0[g] = (int16_t)n;
+      for (uint32_t s = rest;; s = (s - 1) & rest) {
+        if (c_popc(s) == PR && (!SYM || c_rank(m) < c_rank(s))) {
+          t.p[n] = (int16_t)c_rank(s);
+          t.o[n] = (int16_t)c_rank(m | s);
+          ++n;
+        }
+        if (s == 0) break;
+      }
+      ++g;
+    }
+    t.g0[g] = (int16_t)n;
+    return t;
+  }
+  static constexpr Tab tab = make();
+  __host__ __device__ static constexpr int ga(int g) { return tab.ga[g]; }
+  __host__ __device__ static constexpr int g0(int g) { return tab.g0[g]; }
+  __host__ __device__ static constexpr int gn(int g) { return tab.g0[g + 1] - tab.g0[g]; }
+  __host__ __device__ static constexpr int pi(int i) { return tab.p[i]; }
+  __host__ __device__ static constexpr int oi(int i) { return tab.o[i]; }
+};
+template <int V>
+struct CInt {
+  static constexpr int v = V;
+};
+
+template <class PL, int G, int... J>
+__device__ __forceinline__ void ema_reg_group(float a, const float (&p)[PL::NP], float (&o)[PL::NO],
+                                              std::integer_sequence<int, J...>) {
+  ((o[CInt<PL::oi(PL::g0(G) + J)>::v] =
+        fmaf(a, p[CInt<PL::pi(PL::g0(G) + J)>::v], o[CInt<PL::oi(PL::g0(G) + J)>::v])),
+   ...);
+}
+template <class PL, bool SYM, int... G>
+__device__ __forceinline__ void ema_reg_groups(const float* __restrict__ A, int B, const float (&p)[PL::NP],
+                                               float (&o)[PL::NO], std::integer_sequence<int, G...>) {
+  (ema_reg_group<PL, G>(SYM ? p[CInt<PL::ga(G)>::v] : __ldg(A + PL::ga(G) * B), p, o,
+                        std::make_integer_sequence<int, PL::gn(G)>{}),
+   ...);
+}
+template <int... I>
+__device__ __forceinline__ void ema_reg_load(const float* __restrict__ src, int B, float* p,
+                                             std::integer_sequence<int, I...>) {
+  ((p[I] = __ldg(src + I * B)), ...);
+}
+
+template <int K, int AR, int PR, bool SYM>
+__global__ void __launch_bounds__(128, SYM ? 3 : 2) k_ema_reg(const float* __restrict__ Ma, int64_t lda,
+                                                 const float* __restrict__ P, int64_t ldp, float* __restrict__ out,
+                                                 int64_t ldt, int64_t nv, int lb, const ScaleState* st_a,
+                                                 const ScaleState* st_p, ScaleState* st_out) {
+  using PL = EmaRegPlan<K, AR, PR, SYM>;
+  const int B = 1 << lb;
+  const int nsplit = SYM ? c_binom(AR + PR, AR) / 2 : c_binom(AR + PR, AR);
+  const float bound = (float)(SYM ? 2 * nsplit : nsplit) * state_max(st_a) * state_max(st_p);
+  const int s = shift_for(bound);
+  const float scale = (SYM ? 2.f : 1.f) * pow2f(-s);
+  const int64_t rows = nv << lb;
+  float m = 0.f;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = r >> lb;
+    const int b = (int)(r & (B - 1));
+    float p[PL::NP], o[PL::NO];
+    ema_reg_load(P + v * ldp * B + b, B, p, std::make_integer_sequence<int, PL::NP>{});
+#pragma unroll
+    for (int i = 0; i < PL::NO; ++i) o[i] = 0.f;
+    ema_reg_groups<PL, SYM>(Ma + v * lda * B + b, B, p, o, std::make_integer_sequence<int, PL::NA>{});
+    float* dst = out + v * ldt * B + b;
+#pragma unroll
+    for (int i = 0; i < PL::NO; ++i) {
+      const float x = o[i] * scale;
+      dst[(int64_t)i * B] = x;
+      m = fmaxf(m, x);
+    }
+    for (int64_t i = PL::NO; i < ldt; ++i) dst[i * B] = 0.f;
+  }
+  publish_max(st_out, m);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_a->e + st_p->e + s;
+}
+
+// the (K, a-1, p, symmetric) shapes compiled in: the 10-color spider's combine
+// of a 3-vertex leg with the root and another leg (and its symmetric form)
+#define SGC_EMA_REG_SHAPES(X) \
+  X(9, 3, 3, false)           \
+  X(9, 3, 3, true)
+
 // ----------------------------------------------- last step + vertex sum --
 // maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p).  One thread per row
 // r = v * batch + b, rows r, r + S, ... with S (the grid's thread count) a
@@ -1596,9 +1732,29 @@ sgc_status launch_ema_v(const PlanOp& op, const T* Ma, const T* P, T* out, const
   return SGC_OK;
 }
 
+sgc_status launch_ema_reg(const PlanOp& op, const float* Ma, const float* P, float* out, int64_t nv, int lb,
+                          const ScaleState* sa, const ScaleState* sp, ScaleState* so, cudaStream_t st) {
+  const unsigned grid = (unsigned)grid_for(nv << lb, 128, 1 << 30);
+#define SGC_ER(K_, AR_, PR_, SYM_)                                                                           \
+  if (op.ema_reg_k == K_ && op.a - 1 == AR_ && op.p == PR_ && op.ema_sym == SYM_) {                           \
+    k_ema_reg<K_, AR_, PR_, SYM_><<<grid, 128, 0, st>>>(Ma, op.ld_a, P, op.ld_p, out, op.ld_out, nv, lb, sa, sp, \
+                                                        so);                                                  \
+    return SGC_OK;                                                                                           \
+  }
+  SGC_EMA_REG_SHAPES(SGC_ER)
+#undef SGC_ER
+  return fail(SGC_ERR_INTERNAL, "eMA register form not compiled in for this shape");
+}
+
 template <typename T>
 sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows, int lb,
                       const ScaleState* sa, const ScaleState* sp, ScaleState* so, size_t smem_cap, cudaStream_t st) {
+  if (op.ema_reg_k > 0) {
+    if constexpr (std::is_same<T, float>::value)
+      return launch_ema_reg(op, Ma, P, out, rows >> lb, lb, sa, sp, so, st);
+    else
+      return fail(SGC_ERR_INTERNAL, "the register-form eMA is FP32 only");
+  }
   if (op.ema_vrpl > 0) {
     const int64_t nv = rows >> lb;
     const int B = 1 << lb;
@@ -1773,6 +1929,14 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
 }
 
 }  // namespace
+
+bool ema_reg_compiled(int K, int a_minus_1, int p, bool sym) {
+#define SGC_ER(K_, AR_, PR_, SYM_) \
+  if (K == K_ && a_minus_1 == AR_ && p == PR_ && sym == SYM_) return true;
+  SGC_EMA_REG_SHAPES(SGC_ER)
+#undef SGC_ER
+  return false;
+}
 
 sgc_status run_pass(const sgc_graph* g, const Plan& plan, const uint32_t* d_tabs, char* ws, cudaStream_t stream,
                     Profiler* prof, int64_t* kernels) {

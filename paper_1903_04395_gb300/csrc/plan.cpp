@@ -838,8 +838,14 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                  ema_vertex_fits(batch, shape - 100, op.ld_a, op.ld_p, sym, elem, smem_cap)) {
         op.ema_vrpl = shape - 100;
       }
-      op.shape = op.ema_vrpl ? 100 + op.ema_vrpl : op.ema_rows;
       op.ema_sym = op.in_a == op.in_p && A.size - 1 == Pc.size;
+      // the register form (FP32, compiled-in shapes): the default where it exists
+      if (elem == 4 && ema_reg_compiled(K, A.size - 1, Pc.size, op.ema_sym) &&
+          (shape == 0 || shape == kShapeEmaReg)) {
+        op.ema_reg_k = K;
+        op.ema_vrpl = 0;
+      }
+      op.shape = op.ema_reg_k ? kShapeEmaReg : op.ema_vrpl ? 100 + op.ema_vrpl : op.ema_rows;
       if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
       // the vertex-tile kernel takes the raw split indices (rows 0, no column offset)
       op.tab_off = build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
@@ -990,6 +996,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       if ((op.cols_a + op.cols_p) * P.elem * (r + 1) <= smem_cap && c.size() < 5) c.push_back(r);
     for (int v : {1, 2})
       if (ema_vertex_fits(P.batch, v, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap)) c.push_back(100 + v);
+    if (P.elem == 4 && ema_reg_compiled(P.k - 1, op.a - 1, op.p, op.ema_sym)) c.push_back(kShapeEmaReg);
   }
   if (c.size() < 2) c.clear();
   return c;

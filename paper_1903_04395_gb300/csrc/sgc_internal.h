@@ -180,6 +180,7 @@ struct PlanOp {
                              // packed entries staged in shared memory
   int shape = 0;             // launch shape code (kSpmm* / eMA rows), see op_shape_candidates
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
+  int ema_reg_k = 0;         // eMA: > 0 = the register form for K = ema_reg_k relative colors
   int ema_rpl = 1;           // eMA: rows per lane
   int ema_vrpl = 0;          // eMA over vertex tiles (batch >= 4) with 1 or 2 rows per lane; 0 = rows
                              // staged column-major (ema_rows)
@@ -232,8 +233,12 @@ constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
-// eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane)
-constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102;
+// eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane) and the
+// register form (FP32, the (K, a-1, p, symmetric) shapes compiled in)
+constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103;
+// whether the register-form eMA is compiled in for K relative colors, an active
+// child of a vertices (a - 1 colors besides the root's) and a passive child of p
+bool ema_reg_compiled(int K, int a_minus_1, int p, bool sym);
 // entries per lane of the lane-major position table of the batch-specialised
 // direct form (L lanes per coloring; a multiple of 4 so a lane reads 4 at once)
 inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }

@@ -108,7 +108,7 @@ def test_every_spmm_shape(precision, spmm_shape):
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
-@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102])
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102, 103])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_ema_shape(ema_rows, precision):
     sgc.build()
@@ -121,6 +121,37 @@ def test_every_ema_shape(ema_rows, precision):
         seeds = np.arange(20, 45, dtype=np.uint64)
         r = sgc.count(g, t, seeds, precision=precision, ema_rows=ema_rows, batch=16)
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
+
+
+def _two_branch_parent():
+    # DP root 0 with two 3-vertex branches, a path 1-2-3 and a cherry 4-(5, 6): whichever is cut
+    # first, the 7-vertex table combines the P of one branch with the P of the other, a
+    # non-symmetric (a = 4, p = 3) eMA
+    return np.array([-1, 0, 1, 2, 0, 4, 4], dtype=np.int32)
+
+
+@pytest.mark.parametrize("case", ["spider-symmetric", "two-branch-10-colors"])
+def test_register_ema_sums_like_the_vertex_tiles(case):
+    # the register form adds each output's terms in the split table's order: FP32 maps equal
+    # the vertex-tile kernel's bit for bit, and the oracle's within the tolerance
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=8)
+    g = sgc.Graph(rp, ci)
+    if case == "spider-symmetric":
+        parent, colors, root = sgcgen.spider_tree([3, 3, 3]), 0, -1
+    else:
+        parent, colors, root = _two_branch_parent(), 10, 0
+    t = sgc.Template(parent)
+    opt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=8, colors=colors, root=root)
+    rep = sgc.sgc_autotune(g.handle, t.handle, opt)
+    emas = [e for e in rep[:-1] if e["name"] == "ema" and 103 in e["shapes"]]
+    assert any(e["t"] == 7 and e["a"] == 4 and e["p"] == 3 for e in emas), rep
+    seeds = np.arange(60, 76, dtype=np.uint64)
+    a = sgc.count(g, t, seeds, precision="fp32", batch=8, ema_rows=101, colors=colors, root=root)
+    b = sgc.count(g, t, seeds, precision="fp32", batch=8, ema_rows=103, colors=colors, root=root)
+    assert np.array_equal(a.maps, b.maps)
+    ref = oracle.estimate(rp, ci, parent, [int(s) for s in seeds], ncolors=colors or len(parent))
+    assert np.allclose(b.maps, np.array(ref.maps, dtype=np.float64), rtol=FP32_RTOL, atol=0)
 
 
 def test_autotune_report_and_tuned_counts():
