@@ -1369,6 +1369,63 @@ __global__ void __launch_bounds__(kBlock) k_final(const T* __restrict__ Ma, int6
   }
 }
 
+// k_final for a (K, p) compiled in (SGC_FINAL_REG_SHAPES): the active index of
+// each passive color set - the rank of its complement among the K relative
+// colors - is a compile-time constant, so the loop over the C(K, p) sets is
+// fully unrolled with no table loads and the loads of a row are all
+// independent (many in flight per thread).  Same rows per thread, same
+// per-row order and same per-block sums as k_final: the same results.
+template <int K, int PR>
+struct FinalRegPlan {
+  static constexpr int NP = c_binom(K, PR);
+  struct Tab {
+    int16_t ia[NP];
+  };
+  static constexpr Tab make() {
+    Tab t{};
+    const uint32_t full = (1u << K) - 1;
+    for (uint32_t m = 0; m <= full; ++m)
+      if (c_popc(m) == PR) t.ia[c_rank(m)] = (int16_t)c_rank(full & ~m);
+    return t;
+  }
+  static constexpr Tab tab = make();
+  __host__ __device__ static constexpr int ia(int i) { return tab.ia[i]; }
+};
+template <typename T, class FP, int... I>
+__device__ __forceinline__ T final_reg_row(const T* __restrict__ a, const T* __restrict__ p, int lb,
+                                           std::integer_sequence<int, I...>) {
+  const T av[] = {__ldg(a + ((int64_t)CInt<FP::ia(I)>::v << lb))...};
+  const T pv[] = {__ldg(p + ((int64_t)I << lb))...};
+  T part = T(0);
+  ((part += av[I] * pv[I]), ...);
+  return part;
+}
+template <typename T, int K, int PR>
+__global__ void __launch_bounds__(kBlock, 2) k_final_reg(const T* __restrict__ Ma, int64_t lda,
+                                                         const T* __restrict__ P, int64_t ldp, int64_t rows, int lb,
+                                                         double* __restrict__ partials) {
+  using FP = FinalRegPlan<K, PR>;
+  __shared__ double tacc[kBlock];
+  const int batch = 1 << lb;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += S) {
+    const int64_t v = row >> lb, b = row & (batch - 1);
+    acc += (double)final_reg_row<T, FP>(Ma + (v * lda << lb) + b, P + (v * ldp << lb) + b, lb,
+                                        std::make_integer_sequence<int, FP::NP>{});
+  }
+  tacc[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < batch) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += batch) s += tacc[i];
+    partials[(int64_t)blockIdx.x * batch + threadIdx.x] = s;
+  }
+}
+
+// the (K, p) shapes of the last step compiled in: the 10-color spider's
+#define SGC_FINAL_REG_SHAPES(X) X(9, 3)
+
 // last step with a single-vertex active child: maps_b = sum_v P(v, all colors but c(v)),
 // the single entry of the relative P row
 template <typename T>
@@ -1907,10 +1964,22 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, nullptr, S(op.state_p), fp32 ? 1 : 0, outv);
         nk += 2;
         break;
-      case OP_FINAL:
-        k_final<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)), op.ld_a,
-                                                         reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
-                                                         (int)op.cols_p, d_tabs + op.tab_off, rows, lb, partials);
+      case OP_FINAL: {
+        bool done = false;
+#define SGC_FR(K_, PR_)                                                                                      \
+  if (!done && op.final_reg && plan.k - 1 == K_ && op.p == PR_) {                                            \
+    k_final_reg<T, K_, PR_><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)),  \
+                                                                  op.ld_a, reinterpret_cast<const T*>(buf(op.in_p)), \
+                                                                  op.ld_p, rows, lb, partials);                \
+    done = true;                                                                                             \
+  }
+        SGC_FINAL_REG_SHAPES(SGC_FR)
+#undef SGC_FR
+        if (!done)
+          k_final<T><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)), op.ld_a,
+                                                           reinterpret_cast<const T*>(buf(op.in_p)), op.ld_p,
+                                                           (int)op.cols_p, d_tabs + op.tab_off, rows, lb, partials);
+      }
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, S(op.state_a), S(op.state_p), fp32 ? 1 : 0,
                                       outv);
         nk += 2;
@@ -1929,6 +1998,14 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
 }
 
 }  // namespace
+
+bool final_reg_compiled(int K, int p) {
+#define SGC_FR(K_, PR_) \
+  if (K == K_ && p == PR_) return true;
+  SGC_FINAL_REG_SHAPES(SGC_FR)
+#undef SGC_FR
+  return false;
+}
 
 bool ema_reg_compiled(int K, int a_minus_1, int p, bool sym) {
 #define SGC_ER(K_, AR_, PR_, SYM_) \

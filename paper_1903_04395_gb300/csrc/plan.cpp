@@ -480,6 +480,13 @@ static int default_spmm_variant() {
   return v;
 }
 
+// The last step's compile-time form where it is compiled in; SGC_FINAL_TABLE=1
+// keeps the table-driven kernel (same results; read when a plan is made).
+static bool final_reg_enabled() {
+  const char* e = std::getenv("SGC_FINAL_TABLE");
+  return !(e && std::atoi(e) == 1);
+}
+
 // Bucketed SpMM rows the autotuner may try (the planner's own limit is
 // kSpmmBucketMaxBytes): up to 24 KB per warp still keeps 9 warps per SM.
 constexpr int64_t kSpmmBucketTuneMaxBytes = 24 * 1024;
@@ -806,6 +813,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
     }
     if (final) {
       op.kind = A.a < 0 ? OP_FINAL_LEAF : OP_FINAL;
+      op.final_reg = A.a >= 0 && final_reg_compiled(K, Pc.size) && final_reg_enabled();
       op.tab_off = (build_tabs && A.a >= 0) ? build_table(cr, k, OP_FINAL, k, A.size, &P->tabs, &tcache) : 0;
       op.out = P->buf_partials;
       if (A.a < 0) {

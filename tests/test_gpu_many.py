@@ -154,6 +154,21 @@ def test_register_ema_sums_like_the_vertex_tiles(case):
     assert np.allclose(b.maps, np.array(ref.maps, dtype=np.float64), rtol=FP32_RTOL, atol=0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_final_compile_time_form_matches_table_form(monkeypatch, precision):
+    # the last step with compile-time complement indices (the spider's k = 10, p = 3 shape) sums
+    # every row in the table-driven kernel's order: identical maps in either precision
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=12)
+    parent = sgcgen.spider_tree([3, 3, 3])
+    seeds = np.arange(90, 101, dtype=np.uint64)
+    got = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision)
+    monkeypatch.setenv("SGC_FINAL_TABLE", "1")
+    tab = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision)
+    assert np.array_equal(got.maps, tab.maps)
+    check(got.maps, oracle_maps(rp, ci, parent, seeds), precision)
+
+
 def test_autotune_report_and_tuned_counts():
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=5)
