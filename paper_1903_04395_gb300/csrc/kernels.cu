@@ -104,19 +104,33 @@ __global__ void k_color(const int32_t* __restrict__ orig, int64_t n_act, int bat
   }
 }
 
+// color word of vertex x that holds coloring b's byte (8 colorings per word)
+__device__ __forceinline__ uint64_t color_word(const uint8_t* __restrict__ colors, int64_t x, int batch, int word) {
+  const uint8_t* p = colors + x * batch;
+  if (batch >= 8) return __ldg(reinterpret_cast<const unsigned long long*>(p) + word);
+  if (batch == 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
+  if (batch == 2) return __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __ldg(p);
+}
+
 // --------------------------------------- passive single vertex: histogram --
 // P(v, {d}) = number of neighbours of v with color d, for d != c(v), stored at
 // the relative label of d: the SpMM of A with the one-hot leaf table
 // N(u, {x}, {c}) = [c(u) = c], never materialised.  One warp per work item;
 // items are the segments of heavy rows (counted with integer atomics into
 // hist_heavy, by absolute color) followed by the light rows.
-template <typename T>
+// The batch B is a compile-time constant: a neighbour's B color bytes come in
+// one load (or B / 8 for 16 and 32 colorings) and the B counter increments are
+// unrolled.
+template <typename T, int B>
 __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                       const uint8_t* __restrict__ colors, int batch, int k, int32_t n_seg,
+                       const uint8_t* __restrict__ colors, int k, int32_t n_seg,
                        const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo,
                        const int32_t* __restrict__ seg_hi, int32_t n_heavy, int32_t n_act, T* __restrict__ H,
                        int64_t ldh, int32_t* __restrict__ hist_heavy, ScaleState* st_out) {
   extern __shared__ int32_t sh_hist[];
+  constexpr int batch = B;
+  constexpr int NW = B > 8 ? B / 8 : 1, PW = B < 8 ? B : 8;  // color words per vertex, bytes used per word
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bk = batch * k;
   int32_t* h = sh_hist + warp * bk;
@@ -138,8 +152,13 @@ __global__ void k_hist(const int32_t* __restrict__ row_ptr, const int32_t* __res
       hi = row_ptr[row + 1];
     }
     for (int32_t e = lo + lane; e < hi; e += 32) {
-      const uint8_t* cu = colors + (int64_t)__ldg(col_idx + e) * batch;
-      for (int b = 0; b < batch; ++b) atomicAdd(&h[b * k + cu[b]], 1);
+      const int32_t u = __ldg(col_idx + e);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint64_t x = color_word(colors, u, B, w);
+#pragma unroll
+        for (int i = 0; i < PW; ++i) atomicAdd(&h[(w * 8 + i) * k + (int)((x >> (8 * i)) & 0xffu)], 1);
+      }
     }
     __syncwarp();
     if (heavy) {
@@ -228,14 +247,6 @@ __device__ __forceinline__ SpmmItem spmm_item(int64_t item, int32_t n_seg, const
   return it;
 }
 
-// color word of vertex x that holds coloring b's byte (8 colorings per word)
-__device__ __forceinline__ uint64_t color_word(const uint8_t* __restrict__ colors, int64_t x, int batch, int word) {
-  const uint8_t* p = colors + x * batch;
-  if (batch >= 8) return __ldg(reinterpret_cast<const unsigned long long*>(p) + word);
-  if (batch == 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
-  if (batch == 2) return __ldg(reinterpret_cast<const unsigned short*>(p));
-  return __ldg(p);
-}
 
 // One warp per row; see the comment above for the lane mapping and the two
 // forms.  NSMAX > 0: the lane's entries per neighbour (at most NSMAX) live in
@@ -1912,10 +1923,24 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
           SGC_CUDA_TRY(cudaMemsetAsync(hh, 0, sizeof(int32_t) * (size_t)g->n_heavy * B * plan.k, st));
         const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
         const size_t smem = (size_t)(kBlock / 32) * B * plan.k * sizeof(int32_t);
-        allow_smem(k_hist<T>, smem);
-        k_hist<T><<<grid_for(nitems, kBlock / 32, 1 << 30), kBlock, smem, st>>>(
-            g->d_row_ptr, g->d_col_idx, colors, B, plan.k, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi,
-            g->n_heavy, g->n_act, H, op.ld_out, hh, S(op.state_out));
+        const unsigned hgrid = (unsigned)grid_for(nitems, kBlock / 32, 1 << 30);
+#define SGC_HIST(B_)                                                                                          \
+  do {                                                                                                        \
+    allow_smem(k_hist<T, B_>, smem);                                                                          \
+    k_hist<T, B_><<<hgrid, kBlock, smem, st>>>(g->d_row_ptr, g->d_col_idx, colors, plan.k, g->n_seg,          \
+                                               g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act, H, \
+                                               op.ld_out, hh, S(op.state_out));                               \
+  } while (0)
+        switch (B) {
+          case 1: SGC_HIST(1); break;
+          case 2: SGC_HIST(2); break;
+          case 4: SGC_HIST(4); break;
+          case 8: SGC_HIST(8); break;
+          case 16: SGC_HIST(16); break;
+          case 32: SGC_HIST(32); break;
+          default: return fail(SGC_ERR_INTERNAL, "colorings per pass must be a power of two up to 32");
+        }
+#undef SGC_HIST
         ++nk;
         if (g->n_heavy > 0) {
           k_hist_heavy_out<T><<<grid_for((int64_t)g->n_heavy * B * op.ld_out, kBlock, 8 * num_sms), kBlock, 0, st>>>(
