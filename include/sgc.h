@@ -86,7 +86,9 @@ typedef struct sgc_options {
                           asynchronous copies (batch >= 4), 8 / 9 direct specialised for the
                           batch (9: with a lane-major 16-bit position table; 11 / 12: with 8 / 12
                           entries per lane in flight; 13: with a private accumulator column per
-                          lane), 10 bucketed specialised for the batch; ops it does not fit keep
+                          lane; 14: unrolled, one 16-byte position load per lane and neighbour,
+                          4..16 colorings), 10 bucketed specialised for the batch; ops it does not
+                          fit keep
                           theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per

@@ -630,6 +630,108 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
   }
 }
 
+// Direct form, unrolled: the batch B and a bound NS on a lane's entries per
+// neighbour (ns <= NS <= 16) are compile-time constants.  The lane's positions
+// for a neighbour come in one 16-byte load - 8-bit entries, byte q for entry
+// j = jl + L q of the (c_v, c_u) pair, 0xFF = dropped (table OP_SPMM + 600) -
+// instead of one 32-bit lookup per entry through L1, and the next neighbour's
+// id, color, positions and row entries are loaded while the current one is
+// added.  Same summation order as k_spmm_d (a warp barrier between
+// neighbours; a position receives at most one term per neighbour).
+template <typename T, int B, int NS>
+__global__ void __launch_bounds__(kBlock, 5) k_spmm_u(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, const T* __restrict__ Min, int w_in,
+    int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch, const uint4* __restrict__ tab,
+    const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int L = 32 / B;
+  constexpr int NW = B > 8 ? B / 8 : 1;  // color words per vertex
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = ld_out * B;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const int b = lane % B, jl = lane / B;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int64_t row_len = (int64_t)ld_in * B;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = (int)((color_word(colors, it.row, B, word) >> shift) & 0xffu) * k;
+    __syncwarp();
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int cnt = min(32, it.hi - e0);
+      const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+      uint64_t w_lane[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) w_lane[w] = color_word(colors, u_lane, B, w);
+      // neighbour t's positions and entries (loaded one neighbour ahead)
+      auto fetch = [&](int t, uint4& pw, T (&x)[NS]) {
+        const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
+        uint64_t cw = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t y = __shfl_sync(0xffffffffu, w_lane[w], t);
+          if (w == word) cw = y;
+        }
+        const int cu = (int)((cw >> shift) & 0xffu);
+        pw = __ldg(tab + (int64_t)(cvk + cu) * L + jl);
+        const T* src = Min + (int64_t)u * row_len + lane;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) x[q] = q < ns ? __ldg(src + 32 * q) : T(0);
+      };
+      auto add = [&](const uint4& pw, const T (&x)[NS]) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          const uint32_t wq = q < 4 ? pw.x : q < 8 ? pw.y : q < 12 ? pw.z : pw.w;
+          const uint32_t p = (wq >> (8 * (q & 3))) & 0xffu;
+          if (p < (uint32_t)ld_out) acc[p * B + b] += x[q];
+        }
+        __syncwarp();
+      };
+      if (NS <= 4) {  // few entries per lane: keep the next neighbour's loads in flight too
+        uint4 pw;
+        T x[NS];
+        fetch(0, pw, x);
+        for (int t = 0; t < cnt; ++t) {
+          uint4 pn = pw;
+          T xn[NS];
+#pragma unroll
+          for (int q = 0; q < NS; ++q) xn[q] = T(0);
+          if (t + 1 < cnt) fetch(t + 1, pn, xn);
+          add(pw, x);
+          pw = pn;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) x[q] = xn[q];
+        }
+      } else {  // NS loads per lane already in flight per neighbour
+        for (int t = 0; t < cnt; ++t) {
+          uint4 pw;
+          T x[NS];
+          fetch(t, pw, x);
+          add(pw, x);
+        }
+      }
+    }
+    const int out_len = ld_out * B;
+    T* dst = it.heavy ? scratch + item * (int64_t)out_len : P + (int64_t)it.row * out_len;
+    for (int i = lane; i < acc_len; i += 32) {
+      const T v = acc[i];
+      dst[i] = v;
+      if (!it.heavy) m = fmaxf(m, (float)v);
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
 // Bucketed form with the batch B as a compile-time constant: a lane's entries
 // of a neighbour's row are row[l + 32 q] and land in bucket row
 // Q[c(u)][l + 32 q] (no lookup, conflict-free), neighbour ids and color words
@@ -1672,7 +1774,40 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
   } while (0)
-    if (variant == 5 || variant == 6 || variant == 8 || variant == 9 || variant == 10) {
+    if (variant == 11) {
+      const int L = 32 / batch;
+      const int64_t nsmax = (op.cols_p + L - 1) / L;
+      const uint4* tab4 = reinterpret_cast<const uint4*>(tab);
+#define SGC_U(B_, NS_)                                                                                         \
+  do {                                                                                                         \
+    allow_smem(k_spmm_u<T, B_, NS_>, smem);                                                                    \
+    k_spmm_u<T, B_, NS_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                              \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,   \
+        colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab4, si, so);                \
+  } while (0)
+#define SGC_U2(B_)                 \
+  do {                             \
+    if (nsmax <= 3)                \
+      SGC_U(B_, 3);                \
+    else if (nsmax <= 4)           \
+      SGC_U(B_, 4);                \
+    else if (nsmax <= 8)           \
+      SGC_U(B_, 8);                \
+    else if (nsmax <= 9)           \
+      SGC_U(B_, 9);                \
+    else if (nsmax <= 12)          \
+      SGC_U(B_, 12);               \
+    else                           \
+      SGC_U(B_, 16);               \
+  } while (0)
+      if (nsmax > 16 || op.ld_out > 255 || (batch != 4 && batch != 8 && batch != 16))
+        return fail(SGC_ERR_UNSUPPORTED, "unrolled SpMM: needs 4..16 colorings, <= 16 entries per lane, < 255 positions");
+      if (batch == 4) SGC_U2(4);
+      else if (batch == 8) SGC_U2(8);
+      else SGC_U2(16);
+#undef SGC_U2
+#undef SGC_U
+    } else if (variant == 5 || variant == 6 || variant == 8 || variant == 9 || variant == 10) {
 #define SGC_D(B_, LM_, G_)                                                                                   \
   do {                                                                                                       \
     allow_smem(k_spmm_d<T, B_, LM_, G_>, smem);                                                              \

@@ -173,7 +173,8 @@ struct PlanOp {
                              // of 2 / 4 asynchronous row copies, 5 / 6 compile-time batch with
                              // the 32-bit / lane-major 16-bit position table, 8 / 9 compile-time
                              // batch with 8 / 12 entries per lane in flight, 10 private
-                             // accumulator columns;
+                             // accumulator columns, 11 unrolled (8-bit positions, one 16-byte
+                             // load per lane and neighbour);
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -226,11 +227,13 @@ struct Plan {
 // the batch as a compile-time constant (immediate offsets, shuffled ids) with
 // the 32-bit position table or a lane-major 16-bit one, or with 8 / 12 entries
 // per lane in flight (11 / 12), or with one private accumulator column per
-// lane (13, conflict-free adds); likewise the bucketed form (10).
+// lane (13, conflict-free adds), or unrolled over a compile-time bound on a
+// lane's entries with one 16-byte position load per neighbour (14); likewise
+// the bucketed form (10).
 constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3, kShapeSpmmRegBuckets = 4,
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
-              kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13;
+              kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14;
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
@@ -245,6 +248,13 @@ bool final_reg_compiled(int K, int p);
 // entries per lane of the lane-major position table of the batch-specialised
 // direct form (L lanes per coloring; a multiple of 4 so a lane reads 4 at once)
 inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }
+// whether the unrolled direct SpMM (shape 14) takes this op: 4, 8 or 16 colorings, at most 16
+// entries per lane and neighbour, positions below 255
+inline bool spmm_unrolled_fits(int batch, int64_t w_in, int64_t ld_out) {
+  if (batch != 4 && batch != 8 && batch != 16) return false;
+  const int L = 32 / batch;
+  return (w_in + L - 1) / L <= 16 && ld_out < 255;
+}
 // entries per [c_v][c_u] row of the packed position table (rows of whole words)
 inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4 * 4 / eb; }
 
