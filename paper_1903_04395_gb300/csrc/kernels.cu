@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_d(
 // added.  Same summation order as k_spmm_d (a warp barrier between
 // neighbours; a position receives at most one term per neighbour).
 template <typename T, int B, int NS>
-__global__ void __launch_bounds__(kBlock, 5) k_spmm_u(
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 8 && NS > 9 ? 4 : 5) k_spmm_u(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
     const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
     int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, const T* __restrict__ Min, int w_in,

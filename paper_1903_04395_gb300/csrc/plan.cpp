@@ -733,6 +733,13 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_buckets = false;
           op.spmm_variant = 6;
         }
+        if ((batch == 4 || batch == 8) && spmm_unrolled_fits(batch, op.cols_p, op.ld_out) &&
+            !std::getenv("SGC_SPMM_DIRECT")) {
+          // the unrolled direct form where it fits: fastest of all shapes on the R-MAT 20 spider
+          // at 8 colorings (p = 3: 7.5 vs 8.1 ms; p = 2: 2.6 vs 3.4 ms) and at 4 (p = 2)
+          op.spmm_buckets = false;
+          op.spmm_variant = 11;
+        }
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
         if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
           op.spmm_buckets = true;
