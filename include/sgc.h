@@ -87,8 +87,9 @@ typedef struct sgc_options {
                           batch (9: with a lane-major 16-bit position table; 11 / 12: with 8 / 12
                           entries per lane in flight; 13: with a private accumulator column per
                           lane; 14: unrolled, one 16-byte position load per lane and neighbour,
-                          4..16 colorings), 10 bucketed specialised for the batch; ops it does not
-                          fit keep
+                          4..16 colorings; 15: 16-bit positions, one 16-byte load per lane,
+                          neighbour and eight entries, any width), 10 bucketed specialised for the
+                          batch; ops it does not fit keep
                           theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per

@@ -251,7 +251,7 @@ def sgc_count_many(g: int, templates, seeds, opt: sgc_options | None = None):
 SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buckets", 5: "direct+packed", 6: "direct+ring2",
                7: "direct+ring4", 8: "direct-batch",
                9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12",
-               13: "direct-batch-private", 14: "direct-batch-unrolled"}
+               13: "direct-batch-private", 14: "direct-batch-unrolled", 15: "direct-batch-wide"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:

@@ -494,8 +494,8 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
       return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   }
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmUnrolled)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..14");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmWide)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..15");
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != 2 && o.ema_rows != 1 && o.ema_rows != kShapeEmaVertex1 &&
       o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg)

@@ -732,6 +732,92 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 8 && NS > 9 ? 4 : 5) k_sp
   }
 }
 
+// Direct form for wide rows: like k_spmm_u, but with 16-bit positions in
+// chunks of eight - one 16-byte load per lane, neighbour and eight entries
+// (table OP_SPMM + 700: for each (c_v, c_u) pair and lane position jl, nch
+// chunks; 0xFFFF = dropped) - and a runtime chunk count, so any row width
+// works; the row entries of two chunks are loaded together.  Same summation
+// order as k_spmm_d.
+template <typename T, int B>
+__global__ void __launch_bounds__(kBlock) k_spmm_w(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int k, const T* __restrict__ Min, int w_in,
+    int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch, const uint4* __restrict__ tab,
+    const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  constexpr int L = 32 / B;
+  constexpr int NW = B > 8 ? B / 8 : 1;  // color words per vertex
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int acc_len = ld_out * B;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * acc_len;
+  const int b = lane % B, jl = lane / B;
+  const int word = b >> 3, shift = (b & 7) * 8;
+  const int ns = jl < w_in ? (w_in - jl + L - 1) / L : 0;
+  const int nch = ((w_in + L - 1) / L + 7) / 8;  // chunks per lane (the same for every lane)
+  const int64_t row_len = (int64_t)ld_in * B;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t item = blockIdx.x * (int64_t)wpb + warp; item < nitems; item += (int64_t)gridDim.x * wpb) {
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    for (int i = lane; i < acc_len; i += 32) acc[i] = T(0);
+    const int cvk = (int)((color_word(colors, it.row, B, word) >> shift) & 0xffu) * k;
+    __syncwarp();
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int cnt = min(32, it.hi - e0);
+      const int32_t u_lane = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+      uint64_t w_lane[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) w_lane[w] = color_word(colors, u_lane, B, w);
+      for (int t = 0; t < cnt; ++t) {
+        const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
+        uint64_t cw = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint64_t y = __shfl_sync(0xffffffffu, w_lane[w], t);
+          if (w == word) cw = y;
+        }
+        const int cu = (int)((cw >> shift) & 0xffu);
+        const uint4* pt = tab + ((int64_t)(cvk + cu) * L + jl) * nch;
+        const T* src = Min + (int64_t)u * row_len + lane;
+        // two chunks (16 entries) per step: sixteen row loads in flight per lane
+        for (int c = 0; c < nch; c += 2) {
+          const uint4 pa = __ldg(pt + c);
+          const uint4 pb = c + 1 < nch ? __ldg(pt + c + 1) : make_uint4(~0u, ~0u, ~0u, ~0u);
+          T x[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int q = 8 * c + i;
+            x[i] = q < ns ? __ldg(src + 32 * q) : T(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint4& pw = i < 8 ? pa : pb;
+            const int ii = i & 7;
+            const uint32_t wq = ii < 2 ? pw.x : ii < 4 ? pw.y : ii < 6 ? pw.z : pw.w;
+            const uint32_t p = (wq >> (16 * (ii & 1))) & 0xffffu;
+            if (p < (uint32_t)ld_out) acc[p * B + b] += x[i];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    const int out_len = ld_out * B;
+    T* dst = it.heavy ? scratch + item * (int64_t)out_len : P + (int64_t)it.row * out_len;
+    for (int i = lane; i < acc_len; i += 32) {
+      const T v = acc[i];
+      dst[i] = v;
+      if (!it.heavy) m = fmaxf(m, (float)v);
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
 // Bucketed form with the batch B as a compile-time constant: a lane's entries
 // of a neighbour's row are row[l + 32 q] and land in bucket row
 // Q[c(u)][l + 32 q] (no lookup, conflict-free), neighbour ids and color words
@@ -1774,7 +1860,26 @@ sgc_status launch_spmm(const sgc_graph* g, const PlanOp& op, int batch, int k, c
         g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,     \
         colors, batch, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab, si, so);           \
   } while (0)
-    if (variant == 11) {
+    if (variant == 12) {
+      const uint4* tab4 = reinterpret_cast<const uint4*>(tab);
+      if (op.ld_out >= 65535) return fail(SGC_ERR_UNSUPPORTED, "wide SpMM: positions must fit 16 bits");
+#define SGC_W(B_)                                                                                              \
+  do {                                                                                                         \
+    allow_smem(k_spmm_w<T, B_>, smem);                                                                         \
+    k_spmm_w<T, B_><<<grid_for(nitems, wpb, 1 << 30), 32 * wpb, smem, st>>>(                                   \
+        g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, g->d_seg_hi, g->n_heavy, g->n_act,   \
+        colors, k, M, (int)op.cols_p, (int)op.ld_p, P, (int)op.ld_out, scratch, tab4, si, so);                \
+  } while (0)
+      switch (batch) {
+        case 1: SGC_W(1); break;
+        case 2: SGC_W(2); break;
+        case 4: SGC_W(4); break;
+        case 8: SGC_W(8); break;
+        case 16: SGC_W(16); break;
+        default: SGC_W(32); break;
+      }
+#undef SGC_W
+    } else if (variant == 11) {
       const int L = 32 / batch;
       const int64_t nsmax = (op.cols_p + L - 1) / L;
       const uint4* tab4 = reinterpret_cast<const uint4*>(tab);

@@ -332,6 +332,26 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
             }
             tabs->push_back(w);
           }
+  } else if (kind == OP_SPMM + 700) {
+    // wide direct SpMM: for each (c_v, c_u) pair and lane position jl < L = 32 / a
+    // (a = batch), nch chunks of 8 16-bit positions: entry q of the lane's list is
+    // j = jl + L q (0xFFFF = dropped or beyond the row)
+    const int p = t, L = 32 / a;
+    const uint64_t w_in = cr.nsets(p - 1);
+    const int64_t nch = spmm_wide_nch(a, (int64_t)w_in);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
+        for (int jl = 0; jl < L; ++jl)
+          for (int64_t c = 0; c < nch; ++c)
+            for (int wd = 0; wd < 4; ++wd) {
+              uint32_t w = 0;
+              for (int i = 0; i < 2; ++i) {
+                const uint64_t j = (uint64_t)jl + (uint64_t)L * (uint64_t)(8 * c + 2 * wd + i);
+                const uint32_t pos = j < w_in ? spmm_position(cr, k, p, cv, cu, j) : 0xFFFFFFFFu;
+                w |= (pos < 0xFFFFu ? pos : 0xFFFFu) << (16 * i);
+              }
+              tabs->push_back(w);
+            }
   } else if (kind == OP_SPMM + 500) {
     // unpruned combine: [c_v][I_p][c_u] -> the index, in the passive table row of a
     // neighbour u of color c_u, of the p-set I_p (relative to c_v) minus c_u, or ~0
@@ -763,6 +783,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         } else if (shape == kShapeSpmmDirectBLane && op.ld_out < 65535) {
           op.spmm_buckets = false;
           op.spmm_variant = 6;
+        } else if (shape == kShapeSpmmWide && op.ld_out < 65535) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 12;
         } else if (shape == kShapeSpmmUnrolled && spmm_unrolled_fits(batch, op.cols_p, op.ld_out)) {
           op.spmm_buckets = false;
           op.spmm_variant = 11;
@@ -780,7 +803,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_variant = 0;
           op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_variant == 11   ? kShapeSpmmUnrolled
+        op.shape = op.spmm_variant == 12   ? kShapeSpmmWide
+                   : op.spmm_variant == 11 ? kShapeSpmmUnrolled
                    : op.spmm_variant == 10 ? kShapeSpmmDirectBPriv
                    : op.spmm_variant == 9  ? kShapeSpmmDirectB12
                    : op.spmm_variant == 8  ? kShapeSpmmDirectB8
@@ -798,6 +822,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                      : op.spmm_variant == 6  ? build_table(cr, k, (OpKind)(OP_SPMM + 400), Pc.size, 32 / batch,
                                                            &P->tabs, &tcache)
                      : op.spmm_variant == 11 ? build_table(cr, k, (OpKind)(OP_SPMM + 600), Pc.size, batch,
+                                                           &P->tabs, &tcache)
+                     : op.spmm_variant == 12 ? build_table(cr, k, (OpKind)(OP_SPMM + 700), Pc.size, batch,
                                                            &P->tabs, &tcache)
                      : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs,
                                                            &tcache)
@@ -956,6 +982,14 @@ static bool tables_in_range(const Plan& P, int k) {
       const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
       for (int64_t i = 0; i < n; ++i)
         if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
+    } else if (op.kind == OP_SPMM && op.spmm_variant == 12) {
+      const int64_t n = (int64_t)k * k * (32 / P.batch) * spmm_wide_nch(P.batch, op.cols_p) * 4;
+      if (n > left || op.tab_off % 4 != 0) return false;
+      for (int64_t i = 0; i < n; ++i)
+        for (int x = 0; x < 2; ++x) {
+          const uint32_t v = t[i] >> (16 * x) & 0xffffu;
+          if (v != 0xFFFFu && v >= (uint32_t)op.cols_out) return false;
+        }
     } else if (op.kind == OP_SPMM && op.spmm_variant == 11) {
       const int64_t n = (int64_t)k * k * (32 / P.batch) * 4;
       if (n > left || op.tab_off % 4 != 0) return false;
@@ -1025,6 +1059,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
     if (spmm_unrolled_fits(P.batch, op.cols_p, op.ld_out)) c.push_back(kShapeSpmmUnrolled);
+    else if (op.ld_out < 65535) c.push_back(kShapeSpmmWide);
     if (spmm_cols_per_lane(P.batch, op.cols_p) > 4) c.push_back(kShapeSpmmDirectB8);
     if (spmm_cols_per_lane(P.batch, op.cols_p) > 8) c.push_back(kShapeSpmmDirectB12);
     if (op.ld_out * 32 * P.elem <= kSpmmPrivMaxBytes) c.push_back(kShapeSpmmDirectBPriv);

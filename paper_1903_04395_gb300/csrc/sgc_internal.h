@@ -174,7 +174,8 @@ struct PlanOp {
                              // the 32-bit / lane-major 16-bit position table, 8 / 9 compile-time
                              // batch with 8 / 12 entries per lane in flight, 10 private
                              // accumulator columns, 11 unrolled (8-bit positions, one 16-byte
-                             // load per lane and neighbour);
+                             // load per lane and neighbour), 12 wide (16-bit positions, one
+                             // 16-byte load per lane, neighbour and eight entries);
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -228,12 +229,14 @@ struct Plan {
 // the 32-bit position table or a lane-major 16-bit one, or with 8 / 12 entries
 // per lane in flight (11 / 12), or with one private accumulator column per
 // lane (13, conflict-free adds), or unrolled over a compile-time bound on a
-// lane's entries with one 16-byte position load per neighbour (14); likewise
-// the bucketed form (10).
+// lane's entries with one 16-byte position load per neighbour (14), or in
+// chunks of eight 16-bit positions per 16-byte load for any width (15);
+// likewise the bucketed form (10).
 constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 3, kShapeSpmmRegBuckets = 4,
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
-              kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14;
+              kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14,
+              kShapeSpmmWide = 15;
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
@@ -250,6 +253,11 @@ bool final_reg_compiled(int K, int p);
 inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }
 // whether the unrolled direct SpMM (shape 14) takes this op: 4, 8 or 16 colorings, at most 16
 // entries per lane and neighbour, positions below 255
+// chunks of eight entries per lane of the wide direct SpMM (shape 15)
+inline int64_t spmm_wide_nch(int batch, int64_t w_in) {
+  const int L = 32 / batch;
+  return ((w_in + L - 1) / L + 7) / 8;
+}
 inline bool spmm_unrolled_fits(int batch, int64_t w_in, int64_t ld_out) {
   if (batch != 4 && batch != 8 && batch != 16) return false;
   const int L = 32 / batch;
