@@ -40,7 +40,8 @@ def test_bench_workload_against_oracle(rmat20):
     parent = sgcgen.spider_tree([3, 3, 3])
     seeds = list(range(1, 9))
     t = sgc.Template(parent)
-    r32 = sgc.count(g, t, seeds, precision="fp32", batch=8)
+    # the bench's launch configuration: autotuned shapes, 8 colorings in one pass
+    r32 = sgc.count(g, t, seeds, precision="fp32", batch=8, autotune=True)
     r64 = sgc.count(g, t, seeds, precision="fp64", batch=8)
     n = len(rp) - 1
     for i, s in enumerate(seeds):
