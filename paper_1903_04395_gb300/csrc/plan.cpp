@@ -505,10 +505,11 @@ static void use_buf(Plan* P, int buf, int op) {
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
 }
 
-// Direct SpMM loop used when no tuned shape says otherwise: 5 = specialised for
-// the batch (the default: 20-30% faster than the others on R-MAT 20), 0 =
-// chunked with a runtime batch, 1 = next-neighbour prefetch; SGC_SPMM_DIRECT
-// overrides.
+// Direct SpMM loop used when no tuned shape says otherwise and the unrolled
+// form (11, below) does not apply: 5 = specialised for the batch (20-30%
+// faster than the runtime-batch loops on R-MAT 20), 0 = chunked with a runtime
+// batch, 1 = next-neighbour prefetch; SGC_SPMM_DIRECT selects 0, 1 or 5 and
+// also turns the unrolled default off.
 static int default_spmm_variant() {
   static const int v = [] {
     const char* e = std::getenv("SGC_SPMM_DIRECT");
