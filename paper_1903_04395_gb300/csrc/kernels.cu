@@ -1625,6 +1625,61 @@ __global__ void __launch_bounds__(kBlock, 2) k_final_reg(const T* __restrict__ M
 // the (K, p) shapes of the last step compiled in: the 10-color spider's
 #define SGC_FINAL_REG_SHAPES(X) X(9, 3)
 
+// The symmetric register-form eMA fused with the last step that consumes it:
+// the root's table T(v, .) = sum over splits of P(v, A) P(v, S - A) (as in
+// k_ema_reg, in registers, scaled the same way) is never stored; each row's
+// last-step term sum over the p-sets C of T(v, complement of C) P(v, C) is
+// taken from the registers in k_final_reg's order, and the rows' sums go into
+// per-block FP64 partials for k_final_sum.  Rows r = v B + b, r + S, ... with S
+// the grid's thread count (a multiple of B), so a thread keeps one coloring.
+template <class FP, int N, int... I>
+__device__ __forceinline__ float ema_final_row(const float (&o)[N], const float (&p)[N], std::integer_sequence<int, I...>) {
+  float part = 0.f;
+  ((part += o[CInt<FP::ia(I)>::v] * p[I]), ...);
+  return part;
+}
+template <int K, int PR>
+__global__ void __launch_bounds__(128, 3) k_ema_final_reg(const float* __restrict__ P, int64_t ldp, int64_t rows,
+                                                          int lb, const ScaleState* st_p, ScaleState* st_t,
+                                                          double* __restrict__ partials) {
+  using PL = EmaRegPlan<K, PR, PR, true>;
+  using FP = FinalRegPlan<K, PR>;
+  static_assert(PL::NO == FP::NP, "the root table's width is the passive table's");
+  __shared__ double tacc[128];
+  const int B = 1 << lb;
+  const int nsplit = c_binom(2 * PR, PR) / 2;
+  const float bound = (float)(2 * nsplit) * state_max(st_p) * state_max(st_p);
+  const int s = shift_for(bound);
+  const float scale = 2.f * pow2f(-s);
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += S) {
+    const int64_t v = r >> lb;
+    const int b = (int)(r & (B - 1));
+    const float* src = P + v * ldp * B + b;
+    float p[PL::NP], o[PL::NO];
+    ema_reg_load(src, B, p, std::make_integer_sequence<int, PL::NP>{});
+#pragma unroll
+    for (int i = 0; i < PL::NO; ++i) o[i] = 0.f;
+    ema_reg_groups<PL, true>(src, B, p, o, std::make_integer_sequence<int, PL::NA>{});
+#pragma unroll
+    for (int i = 0; i < PL::NO; ++i) o[i] *= scale;
+    acc += (double)ema_final_row<FP>(o, p, std::make_integer_sequence<int, FP::NP>{});
+  }
+  tacc[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < B) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += B) t += tacc[i];
+    partials[(int64_t)blockIdx.x * B + threadIdx.x] = t;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st_t->e = 2 * st_p->e + s;
+}
+
+// the (K, p) shapes of the fused combine + last step compiled in: the 10-color spider's
+#define SGC_EMA_FINAL_SHAPES(X) X(9, 3)
+
+
 // last step with a single-vertex active child: maps_b = sum_v P(v, all colors but c(v)),
 // the single entry of the relative P row
 template <typename T>
@@ -2197,6 +2252,30 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         break;
       }
       case OP_EMA: {
+        if (op.ema_final) {
+          if constexpr (std::is_same<T, float>::value) {
+            bool done = false;
+#define SGC_EF(K_, PR_)                                                                                          \
+  if (!done && op.ema_reg_k == K_ && op.p == PR_) {                                                              \
+    int nb = 0;                                                                                                  \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ema_final_reg<K_, PR_>, 128, 0) != cudaSuccess ||   \
+        nb < 1)                                                                                                  \
+      nb = 1;                                                                                                    \
+    const int grid = std::min(plan.final_blocks, nb * num_sms);                                                  \
+    SGC_CUDA_TRY(cudaMemsetAsync(partials, 0, sizeof(double) * (size_t)plan.final_blocks * B, st));              \
+    k_ema_final_reg<K_, PR_><<<grid, 128, 0, st>>>(reinterpret_cast<const float*>(buf(op.in_p)), op.ld_p, rows,  \
+                                                   lb, S(op.state_p), S(op.state_out), partials);               \
+    done = true;                                                                                                 \
+  }
+            SGC_EMA_FINAL_SHAPES(SGC_EF)
+#undef SGC_EF
+            if (!done) return fail(SGC_ERR_INTERNAL, "fused eMA + last step not compiled in for this shape");
+            ++nk;
+            break;
+          } else {
+            return fail(SGC_ERR_INTERNAL, "the fused eMA + last step is FP32 only");
+          }
+        }
         sgc_status rc = launch_ema<T>(op, reinterpret_cast<const T*>(buf(op.in_a)),
                                       reinterpret_cast<const T*>(buf(op.in_p)), reinterpret_cast<T*>(buf(op.out)),
                                       d_tabs + op.tab_off, rows, lb, S(op.state_a), S(op.state_p), S(op.state_out),
@@ -2230,7 +2309,7 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         nk += 2;
         break;
       case OP_FINAL: {
-        bool done = false;
+        bool done = op.final_fused;  // the fused eMA wrote the partials
 #define SGC_FR(K_, PR_)                                                                                      \
   if (!done && op.final_reg && plan.k - 1 == K_ && op.p == PR_) {                                            \
     k_final_reg<T, K_, PR_><<<plan.final_blocks, kBlock, 0, st>>>(reinterpret_cast<const T*>(buf(op.in_a)),  \
@@ -2263,6 +2342,14 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
 }
 
 }  // namespace
+
+bool ema_final_compiled(int K, int p) {
+#define SGC_EF(K_, PR_) \
+  if (K == K_ && p == PR_) return true;
+  SGC_EMA_FINAL_SHAPES(SGC_EF)
+#undef SGC_EF
+  return false;
+}
 
 bool final_reg_compiled(int K, int p) {
 #define SGC_FR(K_, PR_) \

@@ -956,6 +956,19 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
     use_buf(P, op.in_p, (int)P->ops.size());
     P->ops.push_back(op);
   }
+  // A symmetric register-form eMA whose table only feeds the last step, which
+  // multiplies it with the same passive table: one kernel does both per row
+  // (the eMA's table never goes to HBM).  SGC_NO_FUSE=1 keeps them apart.
+  const size_t nops = P->ops.size();
+  if (nops >= 2 && !(std::getenv("SGC_NO_FUSE") && std::atoi(std::getenv("SGC_NO_FUSE")) == 1)) {
+    PlanOp& e = P->ops[nops - 2];
+    PlanOp& f = P->ops[nops - 1];
+    if (e.kind == OP_EMA && e.ema_reg_k > 0 && e.ema_sym && f.kind == OP_FINAL && f.in_a == e.out &&
+        f.in_p == e.in_p && f.p == e.p && ema_final_compiled(e.ema_reg_k, e.p)) {
+      e.ema_final = true;
+      f.final_fused = true;
+    }
+  }
   P->n_states = n_states;
   P->buf_states = add_buf(P, "states", 8LL * std::max(1, n_states), 0);
   P->scratch_width = max_spmm_width;

@@ -184,6 +184,9 @@ struct PlanOp {
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_reg_k = 0;         // eMA: > 0 = the register form for K = ema_reg_k relative colors
   bool final_reg = false;    // last step: compile-time complement indices (k_final_reg)
+  bool ema_final = false;    // eMA (register form, symmetric) fused with the last step that
+                             // follows it: writes the last step's partials, not its table
+  bool final_fused = false;  // last step done by the preceding fused eMA (only the sum remains)
   int ema_rpl = 1;           // eMA: rows per lane
   int ema_vrpl = 0;          // eMA over vertex tiles (batch >= 4) with 1 or 2 rows per lane; 0 = rows
                              // staged column-major (ema_rows)
@@ -248,6 +251,8 @@ constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103
 bool ema_reg_compiled(int K, int a_minus_1, int p, bool sym);
 // whether the last step's compile-time form is compiled in for K relative colors and a passive child of p
 bool final_reg_compiled(int K, int p);
+// whether the fused symmetric register eMA + last step is compiled in (K, a - 1 = p)
+bool ema_final_compiled(int K, int p);
 // entries per lane of the lane-major position table of the batch-specialised
 // direct form (L lanes per coloring; a multiple of 4 so a lane reads 4 at once)
 inline int64_t spmm_lane_nsp(int64_t w_in, int L) { return ((w_in + L - 1) / L + 3) / 4 * 4; }

@@ -168,9 +168,11 @@ def _two_branch_parent():
 
 
 @pytest.mark.parametrize("case", ["spider-symmetric", "two-branch-10-colors"])
-def test_register_ema_sums_like_the_vertex_tiles(case):
+def test_register_ema_sums_like_the_vertex_tiles(case, monkeypatch):
     # the register form adds each output's terms in the split table's order: FP32 maps equal
-    # the vertex-tile kernel's bit for bit, and the oracle's within the tolerance
+    # the vertex-tile kernel's bit for bit, and the oracle's within the tolerance (the spider's
+    # combine is kept apart from the last step here, as with the vertex tiles)
+    monkeypatch.setenv("SGC_NO_FUSE", "1")
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=8)
     g = sgc.Graph(rp, ci)
@@ -191,6 +193,22 @@ def test_register_ema_sums_like_the_vertex_tiles(case):
     assert np.allclose(b.maps, np.array(ref.maps, dtype=np.float64), rtol=FP32_RTOL, atol=0)
 
 
+def test_fused_combine_and_last_step(monkeypatch):
+    # the spider's symmetric register-form combine fused with the last step: every row's term is
+    # the unfused path's, bit for bit; the rows' FP64 sums run over another grid, so the maps
+    # agree to FP64 rounding, and with the oracle within the FP32 tolerance
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=13)
+    parent = sgcgen.spider_tree([3, 3, 3])
+    for batch, seeds in ((8, np.arange(200, 216, dtype=np.uint64)), (4, np.arange(300, 305, dtype=np.uint64))):
+        fused = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision="fp32", batch=batch)
+        monkeypatch.setenv("SGC_NO_FUSE", "1")
+        apart = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision="fp32", batch=batch)
+        monkeypatch.delenv("SGC_NO_FUSE")
+        assert np.allclose(fused.maps, apart.maps, rtol=1e-12, atol=0), (fused.maps, apart.maps)
+        check(fused.maps, oracle_maps(rp, ci, parent, seeds), "fp32")
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_final_compile_time_form_matches_table_form(monkeypatch, precision):
     # the last step with compile-time complement indices (the spider's k = 10, p = 3 shape) sums
@@ -199,6 +217,7 @@ def test_final_compile_time_form_matches_table_form(monkeypatch, precision):
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=12)
     parent = sgcgen.spider_tree([3, 3, 3])
     seeds = np.arange(90, 101, dtype=np.uint64)
+    monkeypatch.setenv("SGC_NO_FUSE", "1")  # the last step as its own kernel
     got = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision)
     monkeypatch.setenv("SGC_FINAL_TABLE", "1")
     tab = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision)
