@@ -200,7 +200,8 @@ def test_fused_combine_and_last_step(monkeypatch):
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=13)
     parent = sgcgen.spider_tree([3, 3, 3])
-    for batch, seeds in ((8, np.arange(200, 216, dtype=np.uint64)), (4, np.arange(300, 305, dtype=np.uint64))):
+    for batch, seeds in ((8, np.arange(200, 216, dtype=np.uint64)), (4, np.arange(300, 305, dtype=np.uint64)),
+                         (16, np.arange(400, 416, dtype=np.uint64)), (32, np.arange(500, 532, dtype=np.uint64))):
         fused = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision="fp32", batch=batch)
         monkeypatch.setenv("SGC_NO_FUSE", "1")
         apart = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision="fp32", batch=batch)
