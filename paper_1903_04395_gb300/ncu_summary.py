@@ -29,26 +29,47 @@ REPORT_METRICS = [
 ]
 
 
-def launches(path: str) -> None:
+_TIME_MS = {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0}
+_BYTES = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+
+
+def launch_table(path: str) -> dict:
+    """Per kernel (name with template arguments): launches, total ms and, when the capture has them,
+    total DRAM bytes read and written."""
     rows = list(csv.reader(open(path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     h = rows[hi]
     ki, mi, vi, ui = (h.index(x) for x in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
-    agg = collections.defaultdict(lambda: [0, 0.0])
+    agg = collections.defaultdict(lambda: {"launches": 0, "ms": 0.0, "read": 0.0, "write": 0.0})
     for r in rows[hi + 1:]:
-        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+        if len(r) <= vi:
             continue
         m = re.search(r"(k_\w+)(<[^()]*>)?", r[ki])
         key = (m.group(1) + (m.group(2) or "")) if m else r[ki][:60]
         v = float(r[vi].replace(",", ""))
-        scale = {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0}.get(r[ui], 1e-6)
-        agg[key][0] += 1
-        agg[key][1] += v * scale
-    tot = sum(v[1] for v in agg.values())
-    print(f"{'kernel':48s} {'launches':>8s} {'total ms':>10s} {'share':>7s} {'avg ms':>9s}")
-    for k, (n, ms) in sorted(agg.items(), key=lambda x: -x[1][1]):
-        print(f"{k:48s} {n:8d} {ms:10.2f} {100 * ms / tot:6.1f}% {ms / n:9.3f}")
-    print(f"{'total':48s} {sum(v[0] for v in agg.values()):8d} {tot:10.2f}")
+        if r[mi] == "gpu__time_duration.sum":
+            agg[key]["launches"] += 1
+            agg[key]["ms"] += v * _TIME_MS.get(r[ui], 1e-6)
+        elif r[mi] == "dram__bytes_read.sum":
+            agg[key]["read"] += v * _BYTES.get(r[ui], 1.0)
+        elif r[mi] == "dram__bytes_write.sum":
+            agg[key]["write"] += v * _BYTES.get(r[ui], 1.0)
+    return dict(agg)
+
+
+def launches(path: str) -> None:
+    agg = launch_table(path)
+    tot = sum(v["ms"] for v in agg.values())
+    dram = any(v["read"] or v["write"] for v in agg.values())
+    head = f"{'kernel':48s} {'launches':>8s} {'total ms':>10s} {'share':>7s} {'avg ms':>9s}"
+    print(head + (f" {'read GB':>9s} {'write GB':>9s} {'GB/s':>8s}" if dram else ""))
+    for k, v in sorted(agg.items(), key=lambda x: -x[1]["ms"]):
+        n, ms = v["launches"], v["ms"]
+        line = f"{k:48s} {n:8d} {ms:10.2f} {100 * ms / tot:6.1f}% {ms / n:9.3f}"
+        if dram:  # per launch, and their sum over the launch's time
+            line += f" {v['read'] / n / 1e9:9.3f} {v['write'] / n / 1e9:9.3f} {(v['read'] + v['write']) / ms / 1e6:8.0f}"
+        print(line)
+    print(f"{'total':48s} {sum(v['launches'] for v in agg.values()):8d} {tot:10.2f}")
 
 
 def report(paths) -> None:
