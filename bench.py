@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -171,15 +172,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_sha():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1903_04395_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+def kernel_source_sha(function: str):
+    """Hash of one kernel's definition in kernels.cu: from the template line above
+    `__global__ ... <function>(` to the closing brace at the start of a line."""
+    with open(os.path.join(ROOT, "paper_1903_04395_gb300", "csrc", "kernels.cu")) as f:
+        src = f.read()
+    m = re.search(r"\n(template <[^\n]*>\n__global__ void[^\n]*\b" + re.escape(function) + r"\()", src)
+    if not m:
+        return None
+    end = src.find("\n}\n", m.start(1))
+    if end < 0:
+        return None
+    return hashlib.sha256(src[m.start(1):end + 3].encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_name: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the kernel's current
+    source (the record keeps a hash of the kernel function's definition)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -187,7 +196,8 @@ def recorded_traffic(kernel_name: str):
     except Exception:
         return None
     for r in rec.get("kernels", []):
-        if r.get("op") == kernel_name and r.get("kernels_sha") == source_sha():
+        if r.get("op") == kernel_name and r.get("function") and \
+                r.get("function_sha") == kernel_source_sha(r["function"]):
             return r.get("dram_bytes_per_pass")
     return None
 

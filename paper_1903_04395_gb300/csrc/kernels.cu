@@ -2326,7 +2326,7 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
       }
         k_final_sum<<<1, 32, 0, st>>>(partials, plan.final_blocks, B, S(op.state_a), S(op.state_p), fp32 ? 1 : 0,
                                       outv);
-        nk += 2;
+        nk += op.final_fused ? 1 : 2;  // fused: the partials came from the eMA's kernel
         break;
     }
     if (prof) {
