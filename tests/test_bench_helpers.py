@@ -1,0 +1,37 @@
+"""Host-side helpers of bench.py: the traffic record is matched to a kernel by the hash of its
+definition (no GPU)."""
+import importlib.util
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_kernel_source_sha_finds_each_recorded_function():
+    b = _bench()
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    for r in rec["kernels"]:
+        sha = b.kernel_source_sha(r["function"])
+        assert sha is not None and len(sha) == 16
+    assert b.kernel_source_sha("no_such_kernel_anywhere") is None
+
+
+def test_recorded_traffic_follows_the_function_hash(monkeypatch):
+    b = _bench()
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    r = rec["kernels"][0]
+    # with the recorded hash the record is used; with any other hash it reads as unmeasured
+    monkeypatch.setattr(b, "kernel_source_sha", lambda fn: r["function_sha"])
+    assert b.recorded_traffic(r["op"]) == r["dram_bytes_per_pass"]
+    monkeypatch.setattr(b, "kernel_source_sha", lambda fn: "0" * 16)
+    assert b.recorded_traffic(r["op"]) is None
+    assert b.recorded_traffic("no such op") is None
