@@ -361,7 +361,7 @@ class Server:
     def submit(self, template: "Template", seeds, precision: str = "fp32") -> int:
         self.templates[id(template)] = template  # keeps submitted templates alive
         return sgc_server_submit(self.handle, template.handle, seeds,
-                                 SGC_FP64 if precision == "fp64" else SGC_FP32)
+                                 _precision(precision))
 
     def wait(self, ticket: int, n: int, timeout_ms: int = -1):
         return sgc_server_wait(self.handle, ticket, n, timeout_ms)
@@ -445,10 +445,19 @@ class CountResult:
     maps: np.ndarray
 
 
+def _precision(name: str) -> int:
+    """'fp32' or 'fp64' -> sgc_precision; anything else is an error (no silent default)."""
+    if name == "fp32":
+        return SGC_FP32
+    if name == "fp64":
+        return SGC_FP64
+    raise ValueError(f"precision must be 'fp32' or 'fp64', not {name!r}")
+
+
 def count(graph: Graph, template: Template, seeds, precision: str = "fp32", batch: int = 0, root: int = -1,
           mem_limit: int = 0, use_graph: bool = True, autotune: bool = False, spmm_shape: int = 0,
           ema_rows: int = 0, colors: int = 0, unpruned: bool = False) -> CountResult:
-    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root,
+    opt = sgc_options_init(precision=_precision(precision), batch=batch, root=root,
                            mem_limit=mem_limit, use_graph=1 if use_graph else 0, autotune=1 if autotune else 0,
                            spmm_shape=spmm_shape, ema_rows=ema_rows, colors=colors,
                            unpruned=1 if unpruned else 0)
@@ -460,11 +469,11 @@ def count_many(graph: Graph, templates, seeds, precision: str = "fp32", batch: i
                autotune: bool = False, mem_limit: int = 0):
     """Count several templates in one call (one CUDA-graph launch when use_graph): seeds (n_templates, n_iter).
     Returns (estimates, maps[n_templates, n_iter])."""
-    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch,
+    opt = sgc_options_init(precision=_precision(precision), batch=batch,
                            use_graph=1 if use_graph else 0, autotune=1 if autotune else 0, mem_limit=mem_limit)
     return sgc_count_many(graph.handle, [t.handle for t in templates], seeds, opt)
 
 
 def plan(graph: Graph, template: Template, precision: str = "fp32", batch: int = 0, root: int = -1) -> dict:
-    opt = sgc_options_init(precision=SGC_FP64 if precision == "fp64" else SGC_FP32, batch=batch, root=root)
+    opt = sgc_options_init(precision=_precision(precision), batch=batch, root=root)
     return sgc_plan_get(graph.handle, template.handle, opt)

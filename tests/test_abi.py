@@ -97,3 +97,10 @@ def test_iterations_bound_is_the_lemma_count():
         assert abs(got - want) <= 1, (k, eps, delta, got, want)
     for bad in [(0, 0.1, 0.1), (17, 0.1, 0.1), (5, 0.0, 0.1), (5, 0.1, 0.0), (5, 0.1, 1.0)]:
         assert sgc.sgc_iterations_bound(*bad) == -1
+
+
+def test_binding_rejects_unknown_precision():
+    # the binding maps only 'fp32' and 'fp64'; anything else is an error before any call
+    with pytest.raises(ValueError):
+        sgc._precision("fp16")
+    assert sgc._precision("fp32") == sgc.SGC_FP32 and sgc._precision("fp64") == sgc.SGC_FP64
