@@ -267,3 +267,43 @@ def test_more_colors_rejects_too_few():
     rp, ci = sgcgen.er(8, 14, 1)
     with pytest.raises(Exception):
         oracle.count(rp, ci, sgcgen.path_tree(4), oracle.colors(1, 8, 3), ncolors=3)
+
+
+# ------------------------------------------------ the largest intermediate
+# max_intermediate decides whether an FP64 computation of the same DP is exact
+# (every value below 2^53), so it is pinned against enumeration and closed forms.
+
+@pytest.mark.parametrize("name,graph", list(_small_graphs()))
+def test_max_intermediate_brute_force(name, graph):
+    rp, ci = graph
+    n = len(rp) - 1
+    for parent in SMALL_TREES:
+        k = len(parent)
+        if k > 5 or k < 2:
+            continue
+        for cols in [oracle.colors(1, n, k), oracle.colors(2, n, k), np.arange(n) % k]:
+            want = pins.brute_max_intermediate(rp, ci, parent, cols)
+            assert oracle.count(rp, ci, parent, cols).max_intermediate == want, (name, list(parent))
+
+
+def test_max_intermediate_monochrome_is_max_degree():
+    # one color everywhere: no sub-template of two or more vertices is colorful, so every combined
+    # table and the final sum are 0; a leaf's neighbour-sum buffer holds deg(v) at the set {0}
+    rp, ci = sgcgen.rmat(10, edge_factor=8, seed=2)
+    n = len(rp) - 1
+    maxdeg = int(np.diff(rp).max())
+    for parent in [sgcgen.path_tree(3), sgcgen.star_tree(5), sgcgen.pruefer_tree(7, 4)]:
+        r = oracle.count(rp, ci, parent, np.zeros(n, np.uint8))
+        assert r.maps == 0
+        assert r.max_intermediate == max(1, maxdeg)
+
+
+def test_max_intermediate_star_graph_edge_template():
+    # K_{1,m}, hub color 0, leaves color 1, the 2-vertex template: the hub's neighbour sum for {1} is m,
+    # its root-table entry m, each leaf's 1, and the total 2m, the largest value
+    for m in (1, 5, 40):
+        rp, ci = sgcgen.from_edges(m + 1, [(0, i) for i in range(1, m + 1)])
+        cols = np.array([0] + [1] * m, np.uint8)
+        r = oracle.count(rp, ci, sgcgen.path_tree(2), cols)
+        assert r.maps == 2 * m
+        assert r.max_intermediate == 2 * m
