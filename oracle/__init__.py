@@ -6,8 +6,10 @@ shares no code with it (``sgc_oracle.c`` is its own implementation of the
 paper's Section 2.1 color coding, Eq. 1 index, Eq. 2 pruning and the
 pre-computed neighbour traversal of Section 4.2).
 
-Counts are exact unsigned 128-bit integers (overflow is reported, never
-wrapped); Python receives them as ``int``.
+Counts are exact unsigned integers, 128 bits wide; a count that needs more
+is recomputed by the same source compiled with 192-bit limbs
+(``-DORACLE_WIDE``), and only past 192 bits is an overflow reported (never
+wrapped).  Python receives them as ``int``.
 """
 from __future__ import annotations
 
@@ -24,30 +26,39 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sgc_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "libsgc_oracle.so")
+_WIDE_PATH = os.path.join(_HERE, "libsgc_oracle_wide.so")
 _lock = threading.Lock()
 _lib = None
+_wide = None
 
 OK, OVERFLOW, EINVAL, ENOMEM = 0, 1, -1, -2
 
 
 class OracleOverflow(ArithmeticError):
-    """A count exceeded 2**128 - 1."""
+    """A count exceeded the build's range (2**128 - 1, or 2**192 - 1 for the wide build)."""
+
+
+def _build_one(path: str, extra, force: bool) -> str:
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", *extra, "-o", tmp, _SRC])
+        os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile ``libsgc_oracle.so`` in place (gcc -O2 -fopenmp)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile ``libsgc_oracle.so`` (128-bit counts) and ``libsgc_oracle_wide.so`` (192-bit counts)
+    in place (gcc -O2 -fopenmp)."""
+    _build_one(_WIDE_PATH, ["-DORACLE_WIDE"], force)
+    return _build_one(_LIB_PATH, [], force)
 
 
-def _load():
-    global _lib
+def _load(wide: bool = False):
+    global _lib, _wide
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_wide if wide else _lib) is None:
+            build()
+            lib = ctypes.CDLL(_WIDE_PATH if wide else _LIB_PATH)
             P = ctypes.POINTER
             lib.oracle_color.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_uint8)]
             lib.oracle_count.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32,
@@ -62,11 +73,15 @@ def _load():
             lib.oracle_colorset_index.restype = ctypes.c_int64
             lib.oracle_colorset_unindex.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                     P(ctypes.c_int32)]
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             for f in (lib.oracle_color, lib.oracle_count, lib.oracle_count_colors, lib.oracle_automorphisms,
-                      lib.oracle_colorset_unindex, lib.oracle_threads):
+                      lib.oracle_colorset_unindex, lib.oracle_threads, lib.oracle_words, lib.oracle_set_threads):
                 f.restype = ctypes.c_int
-            _lib = lib
-    return _lib
+            if wide:
+                _wide = lib
+            else:
+                _lib = lib
+    return _wide if wide else _lib
 
 
 def _i32(a):
@@ -76,7 +91,7 @@ def _i32(a):
 
 def _check(rc):
     if rc == OVERFLOW:
-        raise OracleOverflow("oracle: a count exceeded the unsigned 128-bit range")
+        raise OracleOverflow("oracle: a count exceeded the build's unsigned integer range")
     if rc == EINVAL:
         raise ValueError("oracle: invalid argument")
     if rc == ENOMEM:
@@ -88,6 +103,12 @@ def _check(rc):
 def threads() -> int:
     """OpenMP threads the oracle uses."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """Use n OpenMP threads in later calls (both builds); returns the previous count."""
+    _load(True).oracle_set_threads(int(n))
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def colors(seed: int, n: int, k: int) -> np.ndarray:
@@ -116,27 +137,39 @@ class CountResult:
     per_vertex: list | None = None
 
 
+def _words(x, w) -> int:
+    return sum(int(x[i]) << (64 * i) for i in range(w))
+
+
 def count(row_ptr, col_idx, parent, cols, mode: str = "pruned", root: int | None = None,
-          per_vertex: bool = False, ncolors: int | None = None) -> CountResult:
+          per_vertex: bool = False, ncolors: int | None = None, wide: bool | None = None) -> CountResult:
     """Exact colorful maps of tree ``parent`` in graph (row_ptr, col_idx) under coloring ``cols``
-    (colors in [0, ncolors), ncolors >= |T|, default |T|: Section 2.1 allows k >= |T| colors)."""
-    lib = _load()
+    (colors in [0, ncolors), ncolors >= |T|, default |T|: Section 2.1 allows k >= |T| colors).
+    wide=None: 128-bit counts, recomputed with 192-bit counts when they overflow; True / False
+    forces one build."""
+    if wide is None:
+        try:
+            return count(row_ptr, col_idx, parent, cols, mode, root, per_vertex, ncolors, wide=False)
+        except OracleOverflow:
+            return count(row_ptr, col_idx, parent, cols, mode, root, per_vertex, ncolors, wide=True)
+    lib = _load(wide)
+    w = int(lib.oracle_words())
     rp, rpp = _i32(row_ptr)
     ci, cip = _i32(col_idx if len(col_idx) else np.zeros(1, np.int32))
     par, parp = _i32(parent)
     col = np.ascontiguousarray(cols, dtype=np.uint8)
     colp = (col if len(col) else np.zeros(1, np.uint8)).ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     n = len(rp) - 1
-    maps = (ctypes.c_uint64 * 2)()
-    mx = (ctypes.c_uint64 * 2)()
-    pv = np.zeros((max(n, 1), 2), dtype=np.uint64) if per_vertex else None
+    maps = (ctypes.c_uint64 * w)()
+    mx = (ctypes.c_uint64 * w)()
+    pv = np.zeros((max(n, 1), w), dtype=np.uint64) if per_vertex else None
     pvp = pv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if per_vertex else None
     rc = lib.oracle_count_colors(n, rpp, cip, len(par), len(par) if ncolors is None else int(ncolors), parp, colp,
                                  {"pruned": 0, "literal": 1}[mode], -1 if root is None else int(root), maps, mx, pvp)
     _check(rc)
-    res = CountResult(maps=int(maps[0]) | (int(maps[1]) << 64), max_intermediate=int(mx[0]) | (int(mx[1]) << 64))
+    res = CountResult(maps=_words(maps, w), max_intermediate=_words(mx, w))
     if per_vertex:
-        res.per_vertex = [int(lo) | (int(hi) << 64) for lo, hi in pv[:n]]
+        res.per_vertex = [_words(row, w) for row in pv[:n]]
     return res
 
 

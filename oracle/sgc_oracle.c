@@ -39,8 +39,13 @@
  *      |T|-subset of colors, and the estimate scales by the inverse of the
  *      probability k! / ((k - |T|)! k^|T|) that a fixed copy is colorful.
  *
- * All counts are exact unsigned 128-bit integers; every add and multiply is
- * overflow-checked and an overflow makes the call return ORACLE_OVERFLOW.
+ * All counts are exact unsigned integers of ORACLE_WORDS 64-bit words: 128
+ * bits by default, 192 bits when compiled with -DORACLE_WIDE (a second
+ * library the Python side falls back to when a count needs more than 128
+ * bits; the paper's Section 7.4 only says floats are used to avoid overflow,
+ * and exact counts of 15-vertex trees on R-MAT graphs of 2^16 vertices
+ * already exceed 2^128).  Every add and multiply is overflow-checked and an
+ * overflow makes the call return ORACLE_OVERFLOW.
  * The largest value seen in any count table, neighbour-sum buffer or the
  * final sum is reported so callers know whether a double-precision
  * computation of the same quantity is exact (all values below 2^53).
@@ -56,6 +61,58 @@
 #endif
 
 typedef unsigned __int128 u128;
+
+/* ---------------- the count type: exact unsigned, overflow-checked ------- */
+
+#ifdef ORACLE_WIDE
+#define ORACLE_WORDS 3
+typedef struct { uint64_t w[3]; } cnt_t;  /* little-endian 64-bit limbs */
+
+static inline cnt_t cnt_small(uint64_t x) { cnt_t r = {{x, 0, 0}}; return r; }
+
+/* r = a + b; returns 1 on overflow past 192 bits */
+static inline int cnt_add(cnt_t a, cnt_t b, cnt_t* r) {
+  u128 c = 0;
+  for (int i = 0; i < 3; ++i) {
+    c += (u128)a.w[i] + b.w[i];
+    r->w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return c != 0;
+}
+
+/* r = a * b; returns 1 when the exact product needs more than 192 bits */
+static inline int cnt_mul(cnt_t a, cnt_t b, cnt_t* r) {
+  uint64_t t[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 3; ++i) {
+    u128 c = 0;
+    for (int j = 0; j < 3; ++j) {
+      c += (u128)a.w[i] * b.w[j] + t[i + j];
+      t[i + j] = (uint64_t)c;
+      c >>= 64;
+    }
+    t[i + 3] = (uint64_t)c;
+  }
+  r->w[0] = t[0]; r->w[1] = t[1]; r->w[2] = t[2];
+  return (t[3] | t[4] | t[5]) != 0;
+}
+
+static inline int cnt_gt(cnt_t a, cnt_t b) {
+  for (int i = 2; i >= 0; --i) if (a.w[i] != b.w[i]) return a.w[i] > b.w[i];
+  return 0;
+}
+
+static inline void cnt_put(cnt_t x, uint64_t* out) { for (int i = 0; i < 3; ++i) out[i] = x.w[i]; }
+#else
+#define ORACLE_WORDS 2
+typedef u128 cnt_t;
+
+static inline cnt_t cnt_small(uint64_t x) { return (cnt_t)x; }
+static inline int cnt_add(cnt_t a, cnt_t b, cnt_t* r) { return __builtin_add_overflow(a, b, r); }
+static inline int cnt_mul(cnt_t a, cnt_t b, cnt_t* r) { return __builtin_mul_overflow(a, b, r); }
+static inline int cnt_gt(cnt_t a, cnt_t b) { return a > b; }
+static inline void cnt_put(cnt_t x, uint64_t* out) { out[0] = (uint64_t)x; out[1] = (uint64_t)(x >> 64); }
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_OVERFLOW 1
@@ -143,7 +200,7 @@ int oracle_colorset_unindex(int64_t idx, int32_t h, int32_t k, int32_t* colors) 
 typedef struct {
   int32_t size;   /* |T_s| */
   int64_t ncols;  /* binom(k, size) */
-  u128* m;        /* n x ncols, row-major: m[v * ncols + I] */
+  cnt_t* m;       /* n x ncols, row-major: m[v * ncols + I] */
 } table;
 
 typedef struct {
@@ -157,22 +214,22 @@ typedef struct {
   int32_t child[ORACLE_MAXK][ORACLE_MAXK];
   int32_t subsize[ORACLE_MAXK];
   int status;
-  u128 max_seen;
+  cnt_t max_seen;
 } dp_ctx;
 
-static void note_max(dp_ctx* ctx, const u128* a, int64_t len) {
-  u128 mx = 0;
-  for (int64_t i = 0; i < len; ++i) if (a[i] > mx) mx = a[i];
-  if (mx > ctx->max_seen) ctx->max_seen = mx;
+static void note_max(dp_ctx* ctx, const cnt_t* a, int64_t len) {
+  cnt_t mx = cnt_small(0);
+  for (int64_t i = 0; i < len; ++i) if (cnt_gt(a[i], mx)) mx = a[i];
+  if (cnt_gt(mx, ctx->max_seen)) ctx->max_seen = mx;
 }
 
 /* leaf table of a single template vertex: N(v,{x},{c}) = [c(v) == c] */
 static int make_leaf(dp_ctx* ctx, table* out) {
   out->size = 1;
   out->ncols = ctx->k;
-  out->m = (u128*)calloc((size_t)ctx->n * (size_t)ctx->k, sizeof(u128));
+  out->m = (cnt_t*)calloc((size_t)ctx->n * (size_t)ctx->k, sizeof(cnt_t));
   if (!out->m && ctx->n > 0) return ORACLE_ENOMEM;
-  for (int32_t v = 0; v < ctx->n; ++v) out->m[(int64_t)v * ctx->k + ctx->colors[v]] = 1;
+  for (int32_t v = 0; v < ctx->n; ++v) out->m[(int64_t)v * ctx->k + ctx->colors[v]] = cnt_small(1);
   if (ctx->n > 0) note_max(ctx, out->m, (int64_t)ctx->n * ctx->k);
   return ORACLE_OK;
 }
@@ -217,22 +274,22 @@ static int combine(dp_ctx* ctx, const table* ma, const table* mp, table* out) {
   if (rc != ORACLE_OK) return rc;
   out->size = t;
   out->ncols = (int64_t)binom(k, t);
-  out->m = (u128*)calloc((size_t)n * (size_t)out->ncols + 1, sizeof(u128));
+  out->m = (cnt_t*)calloc((size_t)n * (size_t)out->ncols + 1, sizeof(cnt_t));
   if (!out->m) { free(s.ia); free(s.ip); return ORACLE_ENOMEM; }
   const int64_t ca = ma->ncols, cp = mp->ncols, cs = out->ncols, ns = s.nsplit;
   int ovf = 0;
 
   if (ctx->mode == 0) {
     /* pruned: P(v, I_p) = sum_{u in N(v)} M_p(u, I_p), once per passive column */
-    u128* P = (u128*)calloc((size_t)n * (size_t)cp + 1, sizeof(u128));
+    cnt_t* P = (cnt_t*)calloc((size_t)n * (size_t)cp + 1, sizeof(cnt_t));
     if (!P) { free(s.ia); free(s.ip); return ORACLE_ENOMEM; }
 #pragma omp parallel for schedule(dynamic, 256) reduction(| : ovf)
     for (int32_t v = 0; v < n; ++v) {
       for (int64_t ip = 0; ip < cp; ++ip) {
-        u128 acc = 0;
+        cnt_t acc = cnt_small(0);
         for (int32_t e = ctx->row_ptr[v]; e < ctx->row_ptr[v + 1]; ++e) {
           int32_t u = ctx->col_idx[e];
-          ovf |= __builtin_add_overflow(acc, mp->m[(int64_t)u * cp + ip], &acc);
+          ovf |= cnt_add(acc, mp->m[(int64_t)u * cp + ip], &acc);
         }
         P[(int64_t)v * cp + ip] = acc;
       }
@@ -241,12 +298,11 @@ static int combine(dp_ctx* ctx, const table* ma, const table* mp, table* out) {
 #pragma omp parallel for schedule(dynamic, 256) reduction(| : ovf)
     for (int32_t v = 0; v < n; ++v) {
       for (int64_t is = 0; is < cs; ++is) {
-        u128 acc = 0;
+        cnt_t acc = cnt_small(0);
         for (int64_t j = 0; j < ns; ++j) {
-          u128 prod;
-          ovf |= __builtin_mul_overflow(ma->m[(int64_t)v * ca + s.ia[is * ns + j]],
-                                        P[(int64_t)v * cp + s.ip[is * ns + j]], &prod);
-          ovf |= __builtin_add_overflow(acc, prod, &acc);
+          cnt_t prod;
+          ovf |= cnt_mul(ma->m[(int64_t)v * ca + s.ia[is * ns + j]], P[(int64_t)v * cp + s.ip[is * ns + j]], &prod);
+          ovf |= cnt_add(acc, prod, &acc);
         }
         out->m[(int64_t)v * cs + is] = acc;
       }
@@ -257,15 +313,15 @@ static int combine(dp_ctx* ctx, const table* ma, const table* mp, table* out) {
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : ovf)
     for (int32_t v = 0; v < n; ++v) {
       for (int64_t is = 0; is < cs; ++is) {
-        u128 acc = 0;
+        cnt_t acc = cnt_small(0);
         for (int64_t j = 0; j < ns; ++j) {
-          const u128 a_val = ma->m[(int64_t)v * ca + s.ia[is * ns + j]];
+          const cnt_t a_val = ma->m[(int64_t)v * ca + s.ia[is * ns + j]];
           const int64_t ip = s.ip[is * ns + j];
           for (int32_t e = ctx->row_ptr[v]; e < ctx->row_ptr[v + 1]; ++e) {
             int32_t u = ctx->col_idx[e];
-            u128 prod;
-            ovf |= __builtin_mul_overflow(a_val, mp->m[(int64_t)u * cp + ip], &prod);
-            ovf |= __builtin_add_overflow(acc, prod, &acc);
+            cnt_t prod;
+            ovf |= cnt_mul(a_val, mp->m[(int64_t)u * cp + ip], &prod);
+            ovf |= cnt_add(acc, prod, &acc);
           }
         }
         out->m[(int64_t)v * cs + is] = acc;
@@ -336,10 +392,6 @@ static int root_template(dp_ctx* ctx, int32_t k, const int32_t* parent, int32_t 
   return root;
 }
 
-static void put_u128(u128 x, uint64_t* out) {
-  out[0] = (uint64_t)x;
-  out[1] = (uint64_t)(x >> 64);
-}
 
 /*
  * Colorful maps of the tree `parent` (t vertices, parent[root] = -1) into the
@@ -350,9 +402,9 @@ static void put_u128(u128 x, uint64_t* out) {
  *   maps = sum_v sum_{C, |C| = t} N(v, T, C).
  *   mode: 0 = pruned (neighbour sums hoisted, Eq. 2), 1 = literal (Algorithm 1 order)
  *   root: template vertex used as the DP root, or -1 for parent's root
- *   maps_out[2]: low/high 64 bits of maps
- *   max_out[2]:  largest value held in any table, buffer or the final sum
- *   per_vertex:  NULL, or n x 2 uint64 receiving sum_C N(v, T, C)
+ *   maps_out[ORACLE_WORDS]: maps, 64-bit words, least significant first
+ *   max_out[ORACLE_WORDS]:  largest value held in any table, buffer or the final sum
+ *   per_vertex:  NULL, or n x ORACLE_WORDS uint64 receiving sum_C N(v, T, C)
  * Returns ORACLE_OK, ORACLE_OVERFLOW, ORACLE_EINVAL or ORACLE_ENOMEM.
  */
 int oracle_count_colors(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t t, int32_t ncolors,
@@ -372,20 +424,20 @@ int oracle_count_colors(int32_t n, const int32_t* row_ptr, const int32_t* col_id
   int rc = subtemplate_table(&ctx, r, 0, &full);
   if (rc != ORACLE_OK) return rc;
   /* full.ncols == binom(ncolors, t): 1 when ncolors == t */
-  u128 maps = 0;
+  cnt_t maps = cnt_small(0);
   int ovf = 0;
   for (int32_t v = 0; v < n; ++v) {
-    u128 row = 0;
-    for (int64_t i = 0; i < full.ncols; ++i) ovf |= __builtin_add_overflow(row, full.m[(int64_t)v * full.ncols + i], &row);
-    ovf |= __builtin_add_overflow(maps, row, &maps);
-    if (row > ctx.max_seen) ctx.max_seen = row;
-    if (per_vertex) put_u128(row, per_vertex + 2 * (int64_t)v);
+    cnt_t row = cnt_small(0);
+    for (int64_t i = 0; i < full.ncols; ++i) ovf |= cnt_add(row, full.m[(int64_t)v * full.ncols + i], &row);
+    ovf |= cnt_add(maps, row, &maps);
+    if (cnt_gt(row, ctx.max_seen)) ctx.max_seen = row;
+    if (per_vertex) cnt_put(row, per_vertex + ORACLE_WORDS * (int64_t)v);
   }
   free(full.m);
   if (ovf) return ORACLE_OVERFLOW;
-  if (maps > ctx.max_seen) ctx.max_seen = maps;
-  put_u128(maps, maps_out);
-  if (max_out) put_u128(ctx.max_seen, max_out);
+  if (cnt_gt(maps, ctx.max_seen)) ctx.max_seen = maps;
+  cnt_put(maps, maps_out);
+  if (max_out) cnt_put(ctx.max_seen, max_out);
   return ORACLE_OK;
 }
 
@@ -421,12 +473,34 @@ int oracle_automorphisms(int32_t k, const int32_t* parent, uint64_t* aut_out) {
     }
   }
   for (int32_t i = 0; i < k; ++i) col[i] = (uint8_t)i;
-  uint64_t maps[2];
+  uint64_t maps[ORACLE_WORDS];
   int rc = oracle_count(k, rp, ci, k, parent, col, 0, -1, maps, NULL, NULL);
   if (rc != ORACLE_OK) return rc;
-  if (maps[1] != 0) return ORACLE_OVERFLOW;
+  for (int i = 1; i < ORACLE_WORDS; ++i) if (maps[i] != 0) return ORACLE_OVERFLOW;
   *aut_out = maps[0];
   return ORACLE_OK;
+}
+
+static int oracle_threads_impl(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* 64-bit words of every count this build returns (2, or 3 with -DORACLE_WIDE) */
+int oracle_words(void) { return ORACLE_WORDS; }
+
+/* OpenMP threads used by later calls (n >= 1); the previous setting is returned */
+int oracle_set_threads(int n) {
+  int old = oracle_threads_impl();
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+  return old;
 }
 
 int oracle_threads(void) {

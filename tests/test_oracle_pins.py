@@ -28,8 +28,10 @@ def _small_graphs():
     yield "hub", sgcgen.from_edges(9, [(0, i) for i in range(1, 7)] + [(1, 2), (2, 3), (3, 7), (7, 8), (8, 5)])
 
 
+@pytest.mark.parametrize("wide", [False, True])
 @pytest.mark.parametrize("name,graph", list(_small_graphs()))
-def test_brute_force_matches_dp(name, graph):
+def test_brute_force_matches_dp(name, graph, wide):
+    # both builds of the oracle: 128-bit counts and 192-bit limbs
     rp, ci = graph
     n = len(rp) - 1
     for parent in SMALL_TREES:
@@ -39,9 +41,9 @@ def test_brute_force_matches_dp(name, graph):
         for seed in (1, 2, 3):
             cols = oracle.colors(seed, n, k)
             want = pins.brute_force_maps(rp, ci, parent, cols)
-            got = oracle.count(rp, ci, parent, cols)
+            got = oracle.count(rp, ci, parent, cols, wide=wide)
             assert got.maps == want, (name, list(parent), seed)
-            assert oracle.count(rp, ci, parent, cols, mode="literal").maps == want
+            assert oracle.count(rp, ci, parent, cols, mode="literal", wide=wide).maps == want
 
 
 def test_brute_force_with_spread_colors():
@@ -273,8 +275,9 @@ def test_more_colors_rejects_too_few():
 # max_intermediate decides whether an FP64 computation of the same DP is exact
 # (every value below 2^53), so it is pinned against enumeration and closed forms.
 
+@pytest.mark.parametrize("wide", [False, True])
 @pytest.mark.parametrize("name,graph", list(_small_graphs()))
-def test_max_intermediate_brute_force(name, graph):
+def test_max_intermediate_brute_force(name, graph, wide):
     rp, ci = graph
     n = len(rp) - 1
     for parent in SMALL_TREES:
@@ -283,7 +286,7 @@ def test_max_intermediate_brute_force(name, graph):
             continue
         for cols in [oracle.colors(1, n, k), oracle.colors(2, n, k), np.arange(n) % k]:
             want = pins.brute_max_intermediate(rp, ci, parent, cols)
-            assert oracle.count(rp, ci, parent, cols).max_intermediate == want, (name, list(parent))
+            assert oracle.count(rp, ci, parent, cols, wide=wide).max_intermediate == want, (name, list(parent))
 
 
 def test_max_intermediate_monochrome_is_max_degree():
@@ -307,3 +310,34 @@ def test_max_intermediate_star_graph_edge_template():
         r = oracle.count(rp, ci, sgcgen.path_tree(2), cols)
         assert r.maps == 2 * m
         assert r.max_intermediate == 2 * m
+
+
+# ---------------------------------------------- counts beyond 128 bits
+# Exact counts of 15-vertex trees on R-MAT graphs of 2^16 vertices exceed 2^128; the oracle then
+# recomputes them with 192-bit limbs.  Pinned by the star closed form past 2^128.
+
+def test_wide_counts_star_closed_form_beyond_128_bits():
+    # K_{1,14} in a star graph whose hub (color 0) has h leaves of each color 1..14: the hub is the
+    # only centre, copies = h^14, maps = 14! * h^14 (|Aut| = 14!), about 2^134 for h = 128
+    h, k = 128, 15
+    leaves = [(0, 1 + c * h + i) for c in range(k - 1) for i in range(h)]
+    rp, ci = sgcgen.from_edges(1 + (k - 1) * h, leaves)
+    cols = np.array([0] + [1 + c for c in range(k - 1) for _ in range(h)], np.uint8)
+    want = math.factorial(k - 1) * h ** (k - 1)
+    assert want > 2 ** 128
+    with pytest.raises(oracle.OracleOverflow):
+        oracle.count(rp, ci, sgcgen.star_tree(k), cols, wide=False)
+    r = oracle.count(rp, ci, sgcgen.star_tree(k), cols)
+    assert r.maps == want
+    assert r.max_intermediate == want
+    assert oracle.count(rp, ci, sgcgen.star_tree(k), cols, wide=True).maps == want
+
+
+def test_wide_equals_narrow_below_128_bits():
+    rp, ci = sgcgen.rmat(10, edge_factor=8, seed=5)
+    n = len(rp) - 1
+    for parent in [sgcgen.pruefer_tree(9, 3), sgcgen.spider_tree([3, 3, 2])]:
+        cols = oracle.colors(4, n, len(parent))
+        a = oracle.count(rp, ci, parent, cols, wide=False, per_vertex=True)
+        b = oracle.count(rp, ci, parent, cols, wide=True, per_vertex=True)
+        assert (a.maps, a.max_intermediate, a.per_vertex) == (b.maps, b.max_intermediate, b.per_vertex)
