@@ -53,8 +53,10 @@ typedef enum sgc_status {
  * FP64. */
 typedef enum sgc_precision { SGC_FP32 = 0, SGC_FP64 = 1 } sgc_precision;
 
-/* Largest template supported: C(16, 8) = 12870 color-set columns. */
-#define SGC_MAX_K 16
+/* Largest number of colors (and template vertices) supported: 18, so that every color set of
+ * the relative-color tables (subsets of the other k - 1 = 17 colors, at most C(17, 8) = 24310 per
+ * row) has a 16-bit index. */
+#define SGC_MAX_K 18
 
 typedef struct sgc_graph sgc_graph;
 typedef struct sgc_template sgc_template;
@@ -89,7 +91,9 @@ typedef struct sgc_options {
                           lane; 14: unrolled, one 16-byte position load per lane and neighbour,
                           4..16 colorings; 15: 16-bit positions, one 16-byte load per lane,
                           neighbour and eight entries, any width), 10 bucketed specialised for the
-                          batch; ops it does not fit keep
+                          batch, 16 grouped (1, 2 or 4 colorings per pass: a warp per row and
+                          coloring sums the rows of each neighbour color in registers and adds each
+                          color's sum into the output row once); ops it does not fit keep
                           theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per
@@ -250,8 +254,8 @@ typedef struct sgc_tune_entry {
   int32_t chosen;            /* index of the kept shape in shapes[] */
   int32_t shapes[8];         /* SpMM: 1 direct, 2 direct with prefetch, 3 bucketed, 4 register buckets,
                                 5 direct with packed positions, 6 / 7 direct with a copy ring,
-                                8 / 9 / 11 / 12 / 13 direct specialised for the batch, 10
-                                bucketed specialised;
+                                8 / 9 / 11 / 12 / 13 / 14 / 15 direct specialised for the batch, 10
+                                bucketed specialised, 16 grouped;
                                 eMA: rows staged per block, or 101 / 102 vertex tiles */
   double ms[8];              /* device time of the op, one pass, per shape */
 } sgc_tune_entry;
@@ -296,6 +300,18 @@ int64_t sgc_iterations_bound(int32_t k, double eps, double delta);
 sgc_status sgc_estimate(const sgc_graph* g, const sgc_template* t, double eps, double delta, uint64_t first_seed,
                         int64_t min_iter, int64_t max_iter, const sgc_options* opt, double* estimate,
                         int64_t* n_used, double* rel_half_width);
+
+/*
+ * The color-coding estimate of Section 2.1 from per-coloring colorful maps
+ * (as sgc_count returns them, e.g. gathered from several processes that each
+ * counted their own seeds): the mean over the n colorings of
+ * maps_i / |Aut(T)| / P(colorful), with P(colorful) = k! / k^k for k = |T|
+ * colors, or k! / ((k - |T|)! k^|T|) for colors = k > |T| (0 = |T|).
+ *   maps      n host doubles, each >= 0
+ *   estimate  out (host); 0 when n = 0
+ */
+sgc_status sgc_estimate_from_maps(const sgc_template* t, int32_t colors, const double* maps, int64_t n,
+                                  double* estimate);
 
 /* --------------------------------------------------------------- serving -- */
 
@@ -389,6 +405,8 @@ typedef struct sgc_op_profile {
   double flops;      /* multiplies + adds of one pass (eMA and final step) */
   double gather_bytes; /* SpMM and histogram: bytes of the neighbour rows gathered in one pass
                           (every stored entry's row once, nnz * row bytes), served by L2 and HBM */
+  int32_t k;           /* colors of the count the op belongs to (ops of different templates with the
+                          same sizes are kept apart) */
 } sgc_op_profile;
 
 /* Turn event recording around every op on (1) or off (0); turning it on

@@ -24,7 +24,7 @@ SGC_ERR_TIMEOUT, SGC_ERR_OVERFLOW, SGC_ERR_INTERNAL, SGC_ERR_UNSUPPORTED = 4, 5,
 SGC_FP32, SGC_FP64 = 0, 1
 SGC_GRAPH_VALIDATE = 1
 SGC_GRAPH_ORDER_RCM = 2
-SGC_MAX_K = 16
+SGC_MAX_K = 18
 
 _STATUS = {0: "SGC_OK", 1: "SGC_ERR_INVALID", 2: "SGC_ERR_OOM", 3: "SGC_ERR_CUDA", 4: "SGC_ERR_TIMEOUT",
            5: "SGC_ERR_OVERFLOW", 6: "SGC_ERR_INTERNAL", 7: "SGC_ERR_UNSUPPORTED"}
@@ -66,7 +66,7 @@ class sgc_op_profile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("t", ctypes.c_int32), ("a", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("passes", ctypes.c_int64), ("kernels", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double),
-                ("gather_bytes", ctypes.c_double)]
+                ("gather_bytes", ctypes.c_double), ("k", ctypes.c_int32)]
 
 
 class sgc_tune_entry(ctypes.Structure):
@@ -106,6 +106,8 @@ SIGNATURES = {
                                     ctypes.c_int64, _P(sgc_options), _P(ctypes.c_double), _P(ctypes.c_int64),
                                     _P(ctypes.c_double)]),
     "sgc_count_device_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _P(sgc_options), _vp]),
+    "sgc_estimate_from_maps": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_double), ctypes.c_int64,
+                                              _P(ctypes.c_double)]),
     "sgc_server_create": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, _P(_vp)]),
     "sgc_server_submit": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_uint64), ctypes.c_int32, ctypes.c_int32,
                                          _P(ctypes.c_uint64)]),
@@ -251,7 +253,8 @@ def sgc_count_many(g: int, templates, seeds, opt: sgc_options | None = None):
 SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buckets", 5: "direct+packed", 6: "direct+ring2",
                7: "direct+ring4", 8: "direct-batch",
                9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12",
-               13: "direct-batch-private", 14: "direct-batch-unrolled", 15: "direct-batch-wide"}
+               13: "direct-batch-private", 14: "direct-batch-unrolled", 15: "direct-batch-wide",
+               16: "grouped"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:
@@ -288,6 +291,15 @@ def sgc_estimate(g: int, t: int, eps: float, delta: float, first_seed: int = 1, 
 
 
 SGC_STATIC_WORKSPACE_BYTES = 64 << 20
+
+
+def sgc_estimate_from_maps(t: int, maps, colors: int = 0) -> float:
+    """The estimate of Section 2.1 from per-coloring colorful maps (computed by libsgc)."""
+    m = np.ascontiguousarray(maps, dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    _check(lib().sgc_estimate_from_maps(t, int(colors), m.ctypes.data_as(_P(ctypes.c_double)), int(m.size),
+                                        ctypes.byref(out)))
+    return float(out.value)
 
 
 def sgc_count_device_static(g: int, t: int, d_seeds: int, n_iter: int, opt: sgc_options | None, d_maps: int) -> None:

@@ -494,8 +494,8 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
       return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   }
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmWide)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0..15");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmGrouped)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0.." + std::to_string(kShapeSpmmGrouped));
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != 2 && o.ema_rows != 1 && o.ema_rows != kShapeEmaVertex1 &&
       o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg)
@@ -909,6 +909,25 @@ sgc_status sgc_autotune(const sgc_graph* g, const sgc_template* t, const sgc_opt
   return SGC_OK;
 }
 
+sgc_status sgc_estimate_from_maps(const sgc_template* t, int32_t colors, const double* maps, int64_t n,
+                                  double* estimate) {
+  if (!t || !estimate || (n > 0 && !maps)) return fail(SGC_ERR_INVALID, "NULL argument");
+  if (n < 0) return fail(SGC_ERR_INVALID, "n must be >= 0");
+  if (colors != 0 && (colors < t->k || colors > SGC_MAX_K))
+    return fail(SGC_ERR_INVALID, "colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
+  if (n == 0) {
+    *estimate = 0.0;
+    return SGC_OK;
+  }
+  long double s = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(maps[i] >= 0.0)) return fail(SGC_ERR_INVALID, "colorful maps must be non-negative numbers");
+    s += (long double)maps[i];
+  }
+  *estimate = (double)(s / (long double)n / (long double)t->aut * inverse_colorful_probability(t->k, colors));
+  return SGC_OK;
+}
+
 sgc_status sgc_profile_enable(const sgc_graph* g, int32_t on) {
   if (!g) return fail(SGC_ERR_INVALID, "graph is NULL");
   std::lock_guard<std::mutex> lock(g->mu);
@@ -951,6 +970,7 @@ sgc_status sgc_profile_read(const sgc_graph* g, sgc_op_profile* out, int32_t cap
     out[i].bytes = a.bytes;
     out[i].flops = a.flops;
     out[i].gather_bytes = a.gather;
+    out[i].k = a.k;
   }
   g->prof.agg.clear();
   return SGC_OK;

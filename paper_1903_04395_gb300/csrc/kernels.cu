@@ -1179,6 +1179,166 @@ __global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_h
   if (std::is_same<T, float>::value) publish_max(st_out, m);
 }
 
+// ---------------------------------------------- neighbours grouped by color --
+// For the grouped SpMM form, per coloring b: the neighbours u of a row (or a
+// heavy-row segment) whose color differs from the row's, grouped by color in
+// ascending order and in CSR order within a color, at ids[b * nnz + lo + i]
+// and cols[b * nnz + lo + i] for i < kept[item * B + b] (lo = the item's first
+// entry).  Neighbours of the row's own color are dropped: every set they hold
+// contains c(v), and v's P row keeps no such set.  A warp per (item,
+// coloring) does a two-pass counting sort of its at most 256 entries (longer
+// rows are cut into segments); colors are below 32.
+template <int B>
+__global__ void __launch_bounds__(kBlock) k_group_nbrs(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_seg,
+    const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi,
+    int32_t n_heavy, int32_t n_act, const uint8_t* __restrict__ colors, int64_t nnz, int32_t* __restrict__ gids,
+    uint8_t* __restrict__ gcols, int32_t* __restrict__ gkept) {
+  __shared__ int cnt_sm[kBlock / 32][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  int* cnt = cnt_sm[warp];
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  for (int64_t w = blockIdx.x * (int64_t)wpb + warp; w < nitems * B; w += (int64_t)gridDim.x * wpb) {
+    const int64_t item = w / B;
+    const int b = (int)(w - item * B);
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    const int cv = colors[(int64_t)it.row * B + b];
+    cnt[lane] = 0;
+    __syncwarp();
+    // pass 1: entries per color
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int32_t e = e0 + lane;
+      const int c = e < it.hi ? (int)colors[(int64_t)__ldg(col_idx + e) * B + b] : cv;
+      const bool keep = c != cv;
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      const unsigned same = __match_any_sync(0xffffffffu, c) & km;
+      if (keep && (same & lt) == 0) cnt[c] += __popc(same);
+      __syncwarp();
+    }
+    // exclusive prefix over the colors (lane = color)
+    const int x = cnt[lane];
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    cnt[lane] = incl - x;
+    __syncwarp();
+    // pass 2: place every kept entry after the earlier ones of its color
+    int32_t* ids = gids + (int64_t)b * nnz + it.lo;
+    uint8_t* cs = gcols + (int64_t)b * nnz + it.lo;
+    for (int32_t e0 = it.lo; e0 < it.hi; e0 += 32) {
+      const int32_t e = e0 + lane;
+      const int32_t u = e < it.hi ? __ldg(col_idx + e) : 0;
+      const int c = e < it.hi ? (int)colors[(int64_t)u * B + b] : cv;
+      const bool keep = c != cv;
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      const unsigned same = __match_any_sync(0xffffffffu, c) & km;
+      if (keep) {
+        const int pos = cnt[c] + __popc(same & lt);
+        ids[pos] = u;
+        cs[pos] = (uint8_t)c;
+      }
+      __syncwarp();
+      if (keep && (same & lt) == 0) cnt[c] += __popc(same);
+      __syncwarp();
+    }
+    if (lane == 0) gkept[w] = total;
+    __syncwarp();
+  }
+}
+
+// Grouped form (one coloring per warp): a warp per (row or heavy-row segment,
+// coloring b) walks the row's neighbours grouped by color (k_group_nbrs).
+// Within a color group every neighbour's entry j lands at the same position
+// of v's row, so the group's rows are summed in registers - lane l holds the
+// entries j = j0 + l + 32 r (r < NR) of a chunk of 32 NR columns, read with
+// coalesced loads - and each group's sum is added once into the output row in
+// shared memory through the 16-bit position table [c_v][c_u][j] (0xFFFF =
+// dropped).  Rows wider than a chunk walk the list once per chunk.  Summation
+// order per position: CSR order within a color, colors ascending (fixed, so
+// results are deterministic).
+template <typename T, int B, int NR>
+__global__ void __launch_bounds__(kBlock) k_spmm_g(
+    const int32_t* __restrict__ row_ptr, int32_t n_seg, const int32_t* __restrict__ seg_row,
+    const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi, int32_t n_heavy, int32_t n_act,
+    const uint8_t* __restrict__ colors, int k, int64_t nnz, const int32_t* __restrict__ gids,
+    const uint8_t* __restrict__ gcols, const int32_t* __restrict__ gkept, const T* __restrict__ Min, int w_in,
+    int ld_in, T* __restrict__ P, int ld_out, T* __restrict__ scratch, const uint16_t* __restrict__ tab,
+    const ScaleState* st_in, ScaleState* st_out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* acc = reinterpret_cast<T*>(sm_raw) + (int64_t)warp * ld_out;
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  float m = 0.f;
+  for (int64_t w = blockIdx.x * (int64_t)wpb + warp; w < nitems * B; w += (int64_t)gridDim.x * wpb) {
+    const int64_t item = w / B;
+    const int b = (int)(w - item * B);
+    const SpmmItem it = spmm_item(item, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    const int cv = colors[(int64_t)it.row * B + b];
+    const int kept = gkept[w];
+    for (int i = lane; i < ld_out; i += 32) acc[i] = T(0);
+    __syncwarp();
+    const int32_t* ids = gids + (int64_t)b * nnz + it.lo;
+    const uint8_t* cs = gcols + (int64_t)b * nnz + it.lo;
+    const uint16_t* tv = tab + (int64_t)cv * k * w_in;
+    for (int j0 = 0; j0 < w_in; j0 += 32 * NR) {
+      const int jl = j0 + lane;
+      T a[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a[r] = T(0);
+      auto flush = [&](int c) {
+        const uint16_t* tp = tv + (int64_t)c * w_in + jl;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (jl + 32 * r < w_in) {
+            const uint32_t pos = __ldg(tp + 32 * r);
+            if (pos != 0xFFFFu) acc[pos] += a[r];
+          }
+          a[r] = T(0);
+        }
+        __syncwarp();
+      };
+      int cur = -1;
+      for (int e0 = 0; e0 < kept; e0 += 32) {
+        const int cnt = min(32, kept - e0);
+        const int32_t u_lane = lane < cnt ? __ldg(ids + e0 + lane) : 0;
+        const int c_lane = lane < cnt ? (int)__ldg(cs + e0 + lane) : 0;
+        for (int t = 0; t < cnt; ++t) {
+          const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
+          const int c = __shfl_sync(0xffffffffu, c_lane, t);
+          if (c != cur) {
+            if (cur >= 0) flush(cur);
+            cur = c;
+          }
+          const T* src = Min + ((int64_t)u * ld_in + jl) * B + b;
+#pragma unroll
+          for (int r = 0; r < NR; ++r)
+            if (jl + 32 * r < w_in) a[r] += __ldg(src + 32 * r * B);
+        }
+      }
+      if (cur >= 0) flush(cur);
+    }
+    T* dst = it.heavy ? scratch + item * (int64_t)ld_out * B : P + (int64_t)it.row * ld_out * B;
+    for (int i = lane; i < ld_out; i += 32) {
+      const T v = acc[i];
+      dst[(int64_t)i * B + b] = v;
+      if (!it.heavy) m = fmaxf(m, (float)v);
+    }
+    __syncwarp();
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
 // ------------------------------------------------------- general eMA --
 // M_s(v, S) = sum over the splits (A, S \ A) of M_a(v, A) * P(v, S \ A).
 // A block stages R consecutive rows of M_a and P in shared memory as
@@ -2146,12 +2306,14 @@ sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const u
   return SGC_OK;
 }
 
-int profile_slot(Profiler* prof, const PlanOp& op, int batch) {
+int profile_slot(Profiler* prof, const PlanOp& op, int batch, int k) {
   for (size_t i = 0; i < prof->agg.size(); ++i) {
     const OpProfile& a = prof->agg[i];
-    if (a.kind == op.kind && a.t == op.t && a.a == op.a && a.p == op.p && a.batch == batch) return (int)i;
+    if (a.kind == op.kind && a.t == op.t && a.a == op.a && a.p == op.p && a.batch == batch && a.k == k)
+      return (int)i;
   }
   OpProfile a;
+  a.k = k;
   a.kind = op.kind;
   a.t = op.t;
   a.a = op.a;
@@ -2162,6 +2324,78 @@ int profile_slot(Profiler* prof, const PlanOp& op, int batch) {
   a.gather = op.gather_bytes;
   prof->agg.push_back(a);
   return (int)prof->agg.size() - 1;
+}
+
+// The grouped SpMM: the color-grouped neighbour lists of the pass (built by the
+// first grouped op), then a warp per (item, coloring) with the chunk width
+// 32 * NR closest above the row width (at most 1024 columns per chunk), then
+// the heavy rows' segment partials summed.
+template <typename T>
+sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanOp& op, int batch,
+                               const uint8_t* colors, const T* M, T* P, T* scratch, const uint32_t* tab,
+                               int32_t* gids, uint8_t* gcols, int32_t* gkept, bool* ready, const ScaleState* si,
+                               ScaleState* so, int num_sms, size_t smem_cap, cudaStream_t st, int64_t* nk) {
+  if (batch != 1 && batch != 2 && batch != 4) return fail(SGC_ERR_INTERNAL, "grouped SpMM: 1, 2 or 4 colorings per pass");
+  if (plan.k > 32 || op.ld_out >= 65535) return fail(SGC_ERR_INTERNAL, "grouped SpMM: shape out of range");
+  if (plan.buf_gids < 0 || plan.buf_gcols < 0 || plan.buf_gkept < 0)
+    return fail(SGC_ERR_INTERNAL, "grouped SpMM: the plan has no neighbour-group buffers");
+  const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+  const int wpb = kBlock / 32;
+  if (!*ready) {
+    const unsigned grid = (unsigned)grid_for(nitems * batch, wpb, 1 << 30);
+#define SGC_GN(B_)                                                                                             \
+  k_group_nbrs<B_><<<grid, kBlock, 0, st>>>(g->d_row_ptr, g->d_col_idx, g->n_seg, g->d_seg_row, g->d_seg_lo, \
+                                             g->d_seg_hi, g->n_heavy, g->n_act, colors, g->nnz, gids, gcols,   \
+                                             gkept)
+    if (batch == 1) SGC_GN(1);
+    else if (batch == 2) SGC_GN(2);
+    else SGC_GN(4);
+#undef SGC_GN
+    ++*nk;
+    *ready = true;
+  }
+  const size_t per_warp = (size_t)op.ld_out * sizeof(T);
+  int w = wpb;
+  while (w > 2 && per_warp * w > smem_cap) w /= 2;
+  if (per_warp * w > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "grouped SpMM: output row does not fit in shared memory");
+  const size_t smem = per_warp * w;
+  const int w_in = (int)op.cols_p;
+  const int need = (w_in + 31) / 32;
+  const int nr = need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : 32;
+  const uint16_t* tab16 = reinterpret_cast<const uint16_t*>(tab);
+  const unsigned grid = (unsigned)grid_for(nitems * batch, w, 1 << 30);
+#define SGC_G(B_, NR_)                                                                                          \
+  do {                                                                                                          \
+    allow_smem(k_spmm_g<T, B_, NR_>, smem);                                                                     \
+    k_spmm_g<T, B_, NR_><<<grid, 32 * w, smem, st>>>(g->d_row_ptr, g->n_seg, g->d_seg_row, g->d_seg_lo,        \
+                                                     g->d_seg_hi, g->n_heavy, g->n_act, colors, plan.k, g->nnz, \
+                                                     gids, gcols, gkept, M, w_in, (int)op.ld_p, P,             \
+                                                     (int)op.ld_out, scratch, tab16, si, so);                   \
+  } while (0)
+#define SGC_G2(B_)                      \
+  do {                                  \
+    switch (nr) {                       \
+      case 2: SGC_G(B_, 2); break;      \
+      case 4: SGC_G(B_, 4); break;      \
+      case 8: SGC_G(B_, 8); break;      \
+      case 16: SGC_G(B_, 16); break;    \
+      default: SGC_G(B_, 32); break;    \
+    }                                   \
+  } while (0)
+  if (batch == 1) SGC_G2(1);
+  else if (batch == 2) SGC_G2(2);
+  else SGC_G2(4);
+#undef SGC_G2
+#undef SGC_G
+  ++*nk;
+  if (g->n_heavy > 0) {
+    constexpr int VN = Vec16<T>::n;
+    const int64_t width = (int64_t)batch * op.ld_out;
+    k_spmm_reduce<T><<<grid_for((int64_t)g->n_heavy * (width / VN), kBlock, 16 * num_sms), kBlock, 0, st>>>(
+        g->d_heavy_seg, g->n_heavy, scratch, width, P, width, so);
+    ++*nk;
+  }
+  return SGC_OK;
 }
 
 template <typename T>
@@ -2188,6 +2422,7 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
 
   if (fp32) SGC_CUDA_TRY(cudaMemsetAsync(states, 0, sizeof(ScaleState) * (size_t)std::max(1, plan.n_states), st));
   int64_t nk = 0;
+  bool grouped_ready = false;  // neighbour lists grouped by color (once per pass, before the first grouped SpMM)
   for (size_t oi = 0; oi < plan.ops.size(); ++oi) {
     const PlanOp& op = plan.ops[oi];
     int slot = -1;
@@ -2198,7 +2433,7 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         if (prof->agg.size() < plan.ops.size()) prof->agg.resize(plan.ops.size());
         slot = (int)oi;
       } else {
-        slot = profile_slot(prof, op, B);
+        slot = profile_slot(prof, op, B, plan.k);
       }
       SGC_CUDA_TRY(cudaEventCreate(&e0));
       SGC_CUDA_TRY(cudaEventCreate(&e1));
@@ -2245,6 +2480,16 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         break;
       }
       case OP_SPMM: {
+        if (op.spmm_variant == 13) {
+          sgc_status rc = launch_spmm_grouped<T>(g, plan, op, B, colors, reinterpret_cast<const T*>(buf(op.in_p)),
+                                                 reinterpret_cast<T*>(buf(op.out)), scratch, d_tabs + op.tab_off,
+                                                 reinterpret_cast<int32_t*>(buf(plan.buf_gids)),
+                                                 reinterpret_cast<uint8_t*>(buf(plan.buf_gcols)),
+                                                 reinterpret_cast<int32_t*>(buf(plan.buf_gkept)), &grouped_ready,
+                                                 S(op.state_p), S(op.state_out), num_sms, smem_cap, st, &nk);
+          if (rc != SGC_OK) return rc;
+          break;
+        }
         sgc_status rc = launch_spmm<T>(g, op, B, plan.k, colors, reinterpret_cast<const T*>(buf(op.in_p)),
                                        reinterpret_cast<T*>(buf(op.out)), scratch, d_tabs + op.tab_off,
                                        S(op.state_p), S(op.state_out), num_sms, smem_cap, st, &nk);

@@ -99,23 +99,27 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
                                          " bytes of scratch for one coloring; the static workspace holds " +
                                          std::to_string(kStaticWorkspaceBytes) + " bytes (use sgc_count_device)");
   const int root = top.root, policy = top.policy;
-  const int64_t tab_bytes = (int64_t)top.tabs.size() * (int64_t)sizeof(uint32_t);  // same for every batch
+  // the index tables depend on the batch (some SpMM forms key them by it), so each candidate
+  // batch is sized with its own tables
   int bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
-    if ((rc = make_plan(g, t, o.precision, root, policy, b, false, &pb, nullptr,
+    if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr,
                         o.colors, o.unpruned != 0)) != SGC_OK) return rc;
-    if (round_up(pb.ws_bytes, 256) + tab_bytes > (int64_t)kStaticWorkspaceBytes) break;
+    if (static_need(pb) > (int64_t)kStaticWorkspaceBytes) break;
     bfit = b;
   }
   for (int32_t i = 0; i < n_iter;) {
     int b = bfit;
     while (b > n_iter - i) b /= 2;
     Plan plan;
-    if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &plan, nullptr,
-                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
-    if (static_need(plan) > (int64_t)kStaticWorkspaceBytes)
-      return fail(SGC_ERR_INTERNAL, "static workspace plan grew beyond its size");
+    for (;;) {
+      if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &plan, nullptr,
+                          o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+      if (static_need(plan) <= (int64_t)kStaticWorkspaceBytes) break;
+      if (b == 1) return fail(SGC_ERR_INTERNAL, "static workspace plan grew beyond its size");
+      b /= 2;  // a smaller pass needs less
+    }
     char* ws = base;
     uint32_t* d_tabs = reinterpret_cast<uint32_t*>(base + round_up(plan.ws_bytes, 256));
     if (!plan.tabs.empty())

@@ -352,6 +352,19 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
               }
               tabs->push_back(w);
             }
+  } else if (kind == OP_SPMM + 800) {
+    // grouped SpMM: 16-bit positions [c_v][c_u][j] for every entry j < w_in of a
+    // neighbour's row (0xFFFF = dropped), two per word
+    const int p = t;
+    const uint64_t w_in = cr.nsets(p - 1);
+    std::vector<uint16_t> h((size_t)(k * k * w_in) + 1, 0xFFFFu);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
+        for (uint64_t j = 0; j < w_in; ++j) {
+          const uint32_t pos = spmm_position(cr, k, p, cv, cu, j);
+          if (pos != 0xFFFFFFFFu) h[(size_t)((int64_t)(cv * k + cu) * (int64_t)w_in + (int64_t)j)] = (uint16_t)pos;
+        }
+    for (size_t i = 0; i + 1 < h.size(); i += 2) tabs->push_back((uint32_t)h[i] | (uint32_t)h[i + 1] << 16);
   } else if (kind == OP_SPMM + 500) {
     // unpruned combine: [c_v][I_p][c_u] -> the index, in the passive table row of a
     // neighbour u of color c_u, of the p-set I_p (relative to c_v) minus c_u, or ~0
@@ -504,6 +517,8 @@ static void use_buf(Plan* P, int buf, int op) {
   P->bufs[buf].first = std::min(P->bufs[buf].first, op);
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
 }
+
+static int64_t smem_cap_of(const sgc_graph* g) { return g->smem_optin > 0 ? g->smem_optin : 227 * 1024; }
 
 // Direct SpMM loop used when no tuned shape says otherwise and the unrolled
 // form (11, below) does not apply: 5 = specialised for the batch (20-30%
@@ -668,6 +683,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   P->bufs.clear();
   P->ops.clear();
   P->tabs.clear();
+  P->buf_gids = P->buf_gcols = P->buf_gkept = -1;
   const int64_t rows = P->rows;
   const int elem = P->elem;
   const double nv = (double)g->n_act, nnz = (double)g->nnz;
@@ -787,6 +803,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         } else if (shape == kShapeSpmmWide && op.ld_out < 65535) {
           op.spmm_buckets = false;
           op.spmm_variant = 12;
+        } else if (shape == kShapeSpmmGrouped && spmm_grouped_fits(batch, op.ld_out, elem, smem_cap_of(g))) {
+          op.spmm_buckets = false;
+          op.spmm_variant = 13;
         } else if (shape == kShapeSpmmUnrolled && spmm_unrolled_fits(batch, op.cols_p, op.ld_out)) {
           op.spmm_buckets = false;
           op.spmm_variant = 11;
@@ -804,7 +823,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_variant = 0;
           op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_variant == 12   ? kShapeSpmmWide
+        op.shape = op.spmm_variant == 13   ? kShapeSpmmGrouped
+                   : op.spmm_variant == 12 ? kShapeSpmmWide
                    : op.spmm_variant == 11 ? kShapeSpmmUnrolled
                    : op.spmm_variant == 10 ? kShapeSpmmDirectBPriv
                    : op.spmm_variant == 9  ? kShapeSpmmDirectB12
@@ -825,6 +845,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                      : op.spmm_variant == 11 ? build_table(cr, k, (OpKind)(OP_SPMM + 600), Pc.size, batch,
                                                            &P->tabs, &tcache)
                      : op.spmm_variant == 12 ? build_table(cr, k, (OpKind)(OP_SPMM + 700), Pc.size, batch,
+                                                           &P->tabs, &tcache)
+                     : op.spmm_variant == 13 ? build_table(cr, k, (OpKind)(OP_SPMM + 800), Pc.size, 0,
                                                            &P->tabs, &tcache)
                      : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs,
                                                            &tcache)
@@ -971,12 +993,21 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   }
   P->n_states = n_states;
   P->buf_states = add_buf(P, "states", 8LL * std::max(1, n_states), 0);
+  bool grouped = false;
+  for (const PlanOp& op : P->ops) grouped |= op.kind == OP_SPMM && op.spmm_variant == 13;
+  if (grouped) {
+    const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
+    P->buf_gids = add_buf(P, "group_ids", 4LL * batch * g->nnz, 0);
+    P->buf_gcols = add_buf(P, "group_colors", (int64_t)batch * g->nnz, 0);
+    P->buf_gkept = add_buf(P, "group_kept", 4LL * batch * nitems, 0);
+  }
   P->scratch_width = max_spmm_width;
   P->buf_scratch = add_buf(P, "spmm_scratch", (int64_t)g->n_seg * max_spmm_width * elem, 0);
   P->buf_hist_heavy = add_buf(P, "hist_heavy", 4LL * g->n_heavy * batch * k, 0);
   const int last = (int)P->ops.size() - 1;
   for (int b : {P->buf_seeds, P->buf_colors, P->buf_out, P->buf_partials, P->buf_states, P->buf_scratch,
-                P->buf_hist_heavy}) {
+                P->buf_hist_heavy, P->buf_gids, P->buf_gcols, P->buf_gkept}) {
+    if (b < 0) continue;
     P->bufs[b].first = 0;
     P->bufs[b].last = last;
   }
@@ -992,6 +1023,12 @@ static bool tables_in_range(const Plan& P, int k) {
     if (op.kind == OP_SPMM && op.spmm_variant == 6) {
       const int L = 32 / P.batch;
       const int64_t n = (int64_t)k * k * L * spmm_lane_nsp(op.cols_p, L);
+      if ((n + 1) / 2 > left) return false;
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
+      for (int64_t i = 0; i < n; ++i)
+        if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
+    } else if (op.kind == OP_SPMM && op.spmm_variant == 13) {
+      const int64_t n = (int64_t)k * k * op.cols_p;
       if ((n + 1) / 2 > left) return false;
       const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
       for (int64_t i = 0; i < n; ++i)
@@ -1069,6 +1106,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
   const PlanOp& op = P.ops[i];
   const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
   if (op.kind == OP_SPMM) {
+    if (spmm_grouped_fits(P.batch, op.ld_out, P.elem, smem_cap)) c.push_back(kShapeSpmmGrouped);
     c.push_back(kShapeSpmmDirect);
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
@@ -1084,7 +1122,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
     }
     if (reg_buckets_fit(P.batch, P.k, op.cols_p, P.elem, g)) c.push_back(kShapeSpmmRegBuckets);
     if (spmm_packed_bytes(P.k, op.cols_p, op.ld_out) > 0) c.push_back(kShapeSpmmPacked);
-    if (P.batch >= 4) {
+    if (P.batch >= 4 && op.cols_p <= 64) {  // the copy rings measured 3-5x slower on wide rows
       c.push_back(kShapeSpmmRing2);
       c.push_back(kShapeSpmmRing4);
     }

@@ -63,7 +63,7 @@ struct ColorIndex {
 // Per-op device time measured with CUDA events recorded on the launching
 // stream around every op of every pass while profiling is on.
 struct OpProfile {
-  int kind = 0, t = 0, a = 0, p = 0, batch = 0;
+  int kind = 0, t = 0, a = 0, p = 0, batch = 0, k = 0;  // k = colors of the op's plan
   int64_t launches = 0;   // passes recorded
   int64_t kernels = 0;    // kernel launches of those passes
   double ms = 0, bytes = 0, flops = 0;  // summed time; algorithmic bytes / flops per pass
@@ -175,7 +175,9 @@ struct PlanOp {
                              // batch with 8 / 12 entries per lane in flight, 10 private
                              // accumulator columns, 11 unrolled (8-bit positions, one 16-byte
                              // load per lane and neighbour), 12 wide (16-bit positions, one
-                             // 16-byte load per lane, neighbour and eight entries);
+                             // 16-byte load per lane, neighbour and eight entries), 13 grouped
+                             // (a warp per row and coloring sums the rows of each neighbour color
+                             // in registers and scatters each color's sum once);
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -216,6 +218,8 @@ struct Plan {
   // fixed buffers
   int buf_colors = -1, buf_seeds = -1, buf_out = -1, buf_states = -1, buf_partials = -1;
   int buf_scratch = -1, buf_hist_heavy = -1;
+  // neighbours grouped by color, per coloring (grouped SpMM form only): ids, colors, kept counts
+  int buf_gids = -1, buf_gcols = -1, buf_gkept = -1;
   int final_blocks = 0;
   int64_t scratch_width = 0;
 };
@@ -239,7 +243,7 @@ constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
               kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14,
-              kShapeSpmmWide = 15;
+              kShapeSpmmWide = 15, kShapeSpmmGrouped = 16;
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
@@ -267,6 +271,12 @@ inline bool spmm_unrolled_fits(int batch, int64_t w_in, int64_t ld_out) {
   if (batch != 4 && batch != 8 && batch != 16) return false;
   const int L = 32 / batch;
   return (w_in + L - 1) / L <= 16 && ld_out < 255;
+}
+// whether the grouped SpMM (shape 16) takes this op: at most 4 colorings per pass (a warp
+// per row and coloring reads the coloring's entries at a stride of `batch`), positions in 16
+// bits, and at least two warps' output rows in shared memory
+inline bool spmm_grouped_fits(int batch, int64_t ld_out, int elem, int64_t smem_cap) {
+  return batch <= 4 && ld_out < 65535 && 2 * ld_out * elem <= smem_cap;
 }
 // entries per [c_v][c_u] row of the packed position table (rows of whole words)
 inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4 * 4 / eb; }

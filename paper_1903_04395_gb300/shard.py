@@ -30,15 +30,12 @@ def rank_seeds(first_seed: int, n_total: int, rank: int, world: int) -> np.ndarr
     return np.arange(first_seed + lo, first_seed + hi, dtype=np.uint64)
 
 
-def estimate_from_maps(maps, k: int, aut: int) -> float:
-    """Mean over colorings of maps / |Aut(T)| * k^k / k! (Section 2.1)."""
-    maps = np.asarray(maps, dtype=np.float64)
-    if maps.size == 0:
-        return 0.0
-    scale = 1.0
-    for i in range(1, k + 1):
-        scale *= k / i
-    return float(maps.mean() / aut * scale)
+def estimate_from_maps(maps, template, colors: int = 0) -> float:
+    """The estimate over all ranks' colorful maps (gathered in seed order), computed by libsgc's
+    sgc_estimate_from_maps for `template` (a Template or its handle)."""
+    from . import sgc_estimate_from_maps
+    handle = getattr(template, "handle", template)
+    return sgc_estimate_from_maps(handle, maps, colors)
 
 
 def gather_maps(local_maps, n_total: int, group=None) -> np.ndarray:

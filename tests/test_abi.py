@@ -70,7 +70,7 @@ def test_template_automorphisms_closed_forms(built):
     ([-1, 2, 1], "cycle"),
     ([-1, 1], "self parent"),
     ([], "empty"),
-    (list(range(-1, 16)), "k above the maximum"),
+    (list(range(-1, 18)), "k above the maximum"),
 ])
 def test_template_rejects_invalid(built, parent, why):
     with pytest.raises(sgc.SgcError) as ei:
@@ -91,11 +91,11 @@ def test_iterations_bound_is_the_lemma_count():
     # the lemma after Lemma 1 (Section 5.1): O(e^k log(1/delta) / eps^2) colorings, constant 1
     import math
     sgc.build()
-    for k, eps, delta in [(5, 0.1, 0.05), (10, 0.05, 0.01), (1, 1.0, 0.5), (16, 0.2, 0.1)]:
+    for k, eps, delta in [(5, 0.1, 0.05), (10, 0.05, 0.01), (1, 1.0, 0.5), (16, 0.2, 0.1), (18, 0.2, 0.1)]:
         want = math.ceil(math.exp(k) * math.log(1 / delta) / eps ** 2)
         got = sgc.sgc_iterations_bound(k, eps, delta)
         assert abs(got - want) <= 1, (k, eps, delta, got, want)
-    for bad in [(0, 0.1, 0.1), (17, 0.1, 0.1), (5, 0.0, 0.1), (5, 0.1, 0.0), (5, 0.1, 1.0)]:
+    for bad in [(0, 0.1, 0.1), (19, 0.1, 0.1), (5, 0.0, 0.1), (5, 0.1, 0.0), (5, 0.1, 1.0)]:
         assert sgc.sgc_iterations_bound(*bad) == -1
 
 
@@ -104,3 +104,33 @@ def test_binding_rejects_unknown_precision():
     with pytest.raises(ValueError):
         sgc._precision("fp16")
     assert sgc._precision("fp32") == sgc.SGC_FP32 and sgc._precision("fp64") == sgc.SGC_FP64
+
+
+def test_estimate_from_maps_matches_the_oracle_estimator(built):
+    # Section 2.1: mean of maps / |Aut(T)| / P(colorful), P = k!/k^k, or k!/((k-|T|)! k^|T|) with more colors
+    import oracle
+    rp, ci = sgcgen.er(60, 200, 9)
+    for parent, colors in ((sgcgen.pruefer_tree(5, 2), 0), (sgcgen.spider_tree([2, 1]), 0), (sgcgen.path_tree(4), 6)):
+        t = sgc.Template(parent)
+        seeds = list(range(1, 9))
+        ref = oracle.estimate(rp, ci, parent, seeds, ncolors=colors or None)
+        got = sgc.sgc_estimate_from_maps(t.handle, np.array(ref.maps, dtype=np.float64), colors)
+        assert got == pytest.approx(ref.mean, rel=1e-13)
+    t = sgc.Template(sgcgen.path_tree(3))
+    assert sgc.sgc_estimate_from_maps(t.handle, np.zeros(0)) == 0.0
+    # 3-path, k = 3: P(colorful) = 3!/3^3 = 2/9, |Aut| = 2: 36 maps -> 36 / 2 * 9 / 2 = 81
+    assert sgc.sgc_estimate_from_maps(t.handle, np.array([36.0])) == pytest.approx(81.0, rel=1e-15)
+    with pytest.raises(sgc.SgcError):
+        sgc.sgc_estimate_from_maps(t.handle, np.array([-1.0]))
+    with pytest.raises(sgc.SgcError):
+        sgc.sgc_estimate_from_maps(t.handle, np.array([1.0]), sgc.SGC_MAX_K + 1)
+
+
+def test_templates_up_to_eighteen_vertices(built):
+    # k <= 18: every relative color set (subsets of the other 17 colors) has a 16-bit index
+    assert sgc.SGC_MAX_K == 18
+    assert sgc.Template(sgcgen.path_tree(18)).automorphisms == 2
+    assert sgc.Template(sgcgen.star_tree(18)).automorphisms == math.factorial(17)
+    assert sgc.Template(sgcgen.pruefer_tree(17, 3)).automorphisms >= 1
+    with pytest.raises(sgc.SgcError):
+        sgc.Template(sgcgen.path_tree(19))

@@ -31,7 +31,23 @@ def test_recorded_traffic_follows_the_function_hash(monkeypatch):
     r = rec["kernels"][0]
     # with the recorded hash the record is used; with any other hash it reads as unmeasured
     monkeypatch.setattr(b, "kernel_source_sha", lambda fn: r["function_sha"])
-    assert b.recorded_traffic(r["op"]) == r["dram_bytes_per_pass"]
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"]) == r["dram_bytes_per_launch"]
+    # another number of colors or colorings per pass is another launch
+    assert b.recorded_traffic(r["op"], r["k"] + 1, r["batch"]) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"] * 2) is None
     monkeypatch.setattr(b, "kernel_source_sha", lambda fn: "0" * 16)
-    assert b.recorded_traffic(r["op"]) is None
-    assert b.recorded_traffic("no such op") is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"]) is None
+    assert b.recorded_traffic("no such op", r["k"], r["batch"]) is None
+
+
+def test_survey_bytes_formulas():
+    # the survey's algorithmic bytes: SpMM 4(n+1+nnz) + 2 b n C(k,p) per coloring, eMA b n (C_a+C_p+C_t)
+    import math
+    b = _bench()
+    n, nnz = 1000, 5000
+    assert b.survey_bytes({"kind": "spmm", "t": 0, "a": 0, "p": 3}, n, nnz, 10, 4, 2) == \
+        4 * (n + 1 + nnz) + 2 * 2 * 4 * n * math.comb(10, 3)
+    assert b.survey_bytes({"kind": "ema", "t": 6, "a": 3, "p": 3}, n, nnz, 10, 4, 1) == \
+        4 * n * (math.comb(10, 3) + math.comb(10, 3) + math.comb(10, 6))
+    assert b.survey_bytes({"kind": "final", "t": 10, "a": 7, "p": 3}, n, nnz, 10, 4, 1) == \
+        4 * n * (math.comb(10, 7) + math.comb(10, 3))

@@ -92,20 +92,41 @@ def test_recorded_sequence_replays_with_new_seeds(er_graph):
     assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
 
 
-@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_spmm_shape(precision, spmm_shape):
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=3)
     g = sgc.Graph(rp, ci)
     assert g.stats()["n_heavy"] > 0  # rows split into segments are covered
-    # register buckets take one coloring per pass
-    batch = 1 if spmm_shape == 4 else 0
+    # register buckets take one coloring per pass, the grouped form at most 4 (passes of 4, 4, 2, 1)
+    batch = 1 if spmm_shape == 4 else 4 if spmm_shape == 16 else 0
     for parent in (sgcgen.pruefer_tree(8, 1008), sgcgen.spider_tree([3, 3, 3]), sgcgen.pruefer_tree(13, 7)):
         t = sgc.Template(parent)
         seeds = np.arange(1, 12 if len(parent) < 13 else 3, dtype=np.uint64)  # 8 + 2 + 1
         r = sgc.count(g, t, seeds, precision=precision, spmm_shape=spmm_shape, batch=batch)
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("batch", [1, 2, 4])
+def test_grouped_spmm(batch, precision):
+    # neighbours grouped by color, each color's rows summed in registers and scattered once: the
+    # oracle's counts (FP64 exactly while below 2^53), equal FP64 maps to the direct form, narrow
+    # and wide rows (the 13-vertex tree) and heavy-row segments
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=6)
+    g = sgc.Graph(rp, ci)
+    assert g.stats()["n_heavy"] > 0
+    for parent in (sgcgen.spider_tree([3, 3, 3]), sgcgen.pruefer_tree(13, 7), sgcgen.path_tree(6)):
+        t = sgc.Template(parent)
+        seeds = np.arange(90, 90 + 2 * batch + 1, dtype=np.uint64)  # passes of batch, batch, 1
+        a = sgc.count(g, t, seeds, precision=precision, spmm_shape=16, batch=batch)
+        if precision == "fp64":
+            b = sgc.count(g, t, seeds, precision=precision, spmm_shape=8, batch=batch)
+            assert np.array_equal(a.maps, b.maps) or np.allclose(a.maps, b.maps, rtol=1e-12, atol=0)
+        few = seeds[: (len(seeds) if len(parent) < 13 else 1)]
+        check(a.maps[: len(few)], oracle_maps(rp, ci, parent, few), precision)
 
 
 @pytest.mark.parametrize("batch", [1, 4, 8, 32])

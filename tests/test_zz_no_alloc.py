@@ -41,12 +41,20 @@ def test_static_matches_allocating_entry_point(torch_cuda, precision):
     stream = torch.cuda.Stream()
     opt = sgc.sgc_options_init(precision=precision, stream=stream.cuda_stream)
     ref = torch.zeros(n_iter, dtype=torch.float64, device="cuda")
+    outs = [torch.full((n_iter,), -1.0, dtype=torch.float64, device="cuda") for _ in range(2)]
+    # the inputs were written on torch's current stream; the library reads them on `stream`
+    stream.wait_stream(torch.cuda.current_stream())
     sgc.sgc_count_device(g.handle, t.handle, seeds.data_ptr(), n_iter, opt, ref.data_ptr())
     stream.synchronize()
     ref_h = ref.cpu().numpy()
     for call in range(2):
-        out = torch.full((n_iter,), -1.0, dtype=torch.float64, device="cuda")
+        out = outs[call]
+        free0 = torch.cuda.mem_get_info()[0]
         sgc.sgc_count_device_static(g.handle, t.handle, seeds.data_ptr(), n_iter, opt, out.data_ptr())
+        if call == 1:
+            # nothing was allocated on the device by the call (the first call of the process may
+            # load the module that holds the static array)
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         if precision == sgc.SGC_FP64:
             assert np.array_equal(got, ref_h), (call, got, ref_h)
