@@ -50,9 +50,8 @@ WORKLOADS = {
                          "graph in one sgc_count_many call = one CUDA-graph launch; autotuned launch shapes"),
     "ablation": dict(scale=16, templates=[("spider10", ("spider", [3, 3, 3])), ("pruefer8", ("pruefer", 8, 1008))],
                      batch=8, fp64=False, steps=3, warmup=3,
-                     desc="pruning ablation: the same colorings counted with the SpMM + eMA path (neighbour sums "
-                          "once per passive color set, Eq. 2) and in Algorithm 1's loop order (sums taken again per "
-                          "color set and split), R-MAT scale 16"),
+                     desc="the paper's three variants on the same colorings: SpMM + eMA (PGBSC), pruned neighbour "
+                          "sums one column at a time (PFASCIA), Algorithm 1's loop order (FASCIA), R-MAT scale 16"),
     "rmat21-trees": dict(scale=21, templates=[("path12", ("path", 12)), ("pruefer13", ("pruefer", 13, 7)),
                                               ("pruefer15", ("pruefer", 15, 9))], batch=4, fp64=False,
                          steps=8, warmup=3, cpu_scale=14, cpu_scale_1t=11, ref_scale=13,
@@ -62,6 +61,7 @@ WORKLOADS = {
 
 
 WORKLOAD_SCALE = {name: wl["scale"] for name, wl in WORKLOADS.items()}
+WORKLOAD_TEMPLATES = {name: [n for n, _ in wl["templates"]] for name, wl in WORKLOADS.items()}
 
 
 def parse():
@@ -76,11 +76,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=32, help="serving workload: queries in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: offered queries per second")
+    ap.add_argument("--sweep", default="", help="serving workload: comma-separated offered rates to sweep")
+    ap.add_argument("--sweep-queries", type=int, default=64, help="serving workload: queries per swept rate")
     ap.add_argument("--no-autotune", action="store_true", help="planner launch shapes instead of the autotuner's")
     ap.add_argument("--scale", type=int, default=None,
                     help="R-MAT scale override (small cases for profiling; not a bench configuration)")
     ap.add_argument("--batch", type=int, default=None, help="colorings per pass override")
     ap.add_argument("--spmm-shape", type=int, default=0, help="force an SpMM launch shape (sgc_options.spmm_shape)")
+    ap.add_argument("--ema-rows", type=int, default=0, help="force an eMA launch shape (sgc_options.ema_rows)")
+    ap.add_argument("--template", action="append", default=None,
+                    help="only these templates of the workload (profiling small cases; not a bench configuration)")
     ap.add_argument("--rcm", action="store_true",
                     help="number the graph's rows in reverse Cuthill-McKee order (SGC_GRAPH_ORDER_RCM)")
     args = ap.parse_args()
@@ -89,6 +94,10 @@ def parse():
         wl["scale"] = args.scale
     if args.batch is not None:
         wl["batch"] = args.batch
+    if args.template:
+        wl["templates"] = [(n, sp) for n, sp in wl["templates"] if n in args.template]
+        if not wl["templates"]:
+            ap.error("--template names none of the workload's templates")
     if args.steps is None:
         args.steps = wl.get("steps", 30)
     if args.warmup is None:
@@ -370,8 +379,10 @@ def run_reference(args, wl, rank, world):
 
 
 def config_of(wl, world):
-    return {"workload": args_workload_name(wl) + ("" if wl["scale"] == WORKLOAD_SCALE.get(args_workload_name(wl))
-                                                  else f" (scale {wl['scale']} override)"),
+    name = args_workload_name(wl)
+    subset = [n for n, _ in wl["templates"]] != WORKLOAD_TEMPLATES.get(name)
+    return {"workload": name + ("" if wl["scale"] == WORKLOAD_SCALE.get(name) else f" (scale {wl['scale']} override)")
+            + (f" (templates {','.join(n for n, _ in wl['templates'])} only)" if subset else ""),
             "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
             % wl["scale"], "templates": [name for name, _ in wl["templates"]], "k": "|T|",
             "colorings_per_step_per_gpu": wl["batch"] * len(wl["templates"]),
@@ -387,34 +398,22 @@ def args_workload_name(wl):
     return _WL_NAME.get(id(wl), "rmat20-spider10")
 
 
-def run_serving(args, wl, rank, world, local):
-    """Continuous-batching server over a resident graph fed by a Poisson query stream."""
-    import torch
-    import paper_1903_04395_gb300 as sgc
+def serve_stream(sgc, g, Q, rate, base, warm=True):
+    """One Poisson stream of Q queries (Pruefer trees of 3..14 vertices, 1..32 colorings) offered at `rate`
+    queries/s to a fresh server (120 GB budget, 8 slots); returns the stream's measurements."""
     import sgcgen
-    torch.cuda.set_device(local)
-    if rank == 0:
-        sgc.build()
-    sgc.lib()
-    rp, ci = make_graph(wl)
-    n, nnz = len(rp) - 1, len(ci)
-    d_rp = torch.from_numpy(rp).cuda()
-    d_ci = torch.from_numpy(ci).cuda()
-    g = sgc.Graph.from_device(n, nnz, d_rp.data_ptr(), d_ci.data_ptr())
-    Q = args.queries
-    base = 1000 * (rank + 1)
     sizes = sgcgen.uniform_ints(3, 14, Q, seed=base + 11)
     ncol = sgcgen.uniform_ints(1, 32, Q, seed=base + 12)
-    arrivals = sgcgen.poisson_arrivals(args.rate, Q, seed=base + 5)
+    arrivals = sgcgen.poisson_arrivals(rate, Q, seed=base + 5)
     tpls = [sgc.Template(sgcgen.pruefer_tree(int(sizes[q]), base + q)) for q in range(Q)]
+    if warm:
+        # one small query of every size (plans, tables, module loading)
+        srv = sgc.Server(g, 120 << 30, 8)
+        for kk in range(3, 15):
+            w = sgc.Template(sgcgen.pruefer_tree(kk, 77))
+            srv.wait(srv.submit(w, [1]), 1)
+        srv.close()
     srv = sgc.Server(g, 120 << 30, 8)
-    # warm-up: one small query of every size (plans, tables, module loading)
-    for kk in range(3, 15):
-        w = sgc.Template(sgcgen.pruefer_tree(kk, 77))
-        srv.wait(srv.submit(w, [1]), 1)
-    srv.close()
-    srv = sgc.Server(g, 120 << 30, 8)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
     tickets = []
     for q in range(Q):
@@ -431,27 +430,58 @@ def run_serving(args, wl, rank, world, local):
     st = srv.stats()
     srv.close()
     colorings = int(np.sum(ncol))
-    value = colorings / span
-    res = {"metric": METRIC, "value": value * world, "unit": "colorings/s", "n_gpus": world, "steps": Q,
-           "warmup": 12, "ms_per_step": 1e3 * span / Q, "higher_is_better": True, "scaling": "weak",
+    return {"offered_qps": rate, "queries": Q, "achieved_qps": Q / span, "colorings_per_s": colorings / span,
+            "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": st["queue_p50_ms"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
+            "colorings": colorings, "span_s": span, "kernel_launches": st["kernel_launches"]}
+
+
+def run_serving(args, wl, rank, world, local):
+    """Continuous-batching server over a resident graph fed by Poisson query streams: the configured
+    stream (--queries at --rate), and with --sweep a stream of --sweep-queries at each of several offered
+    rates (offered vs achieved rate and p50 / p99 latency per rate; the sustainable rate is the highest
+    offered rate the server keeps up with, achieved >= 90% of offered)."""
+    import torch
+    import paper_1903_04395_gb300 as sgc
+    torch.cuda.set_device(local)
+    if rank == 0:
+        sgc.build()
+    sgc.lib()
+    rp, ci = make_graph(wl)
+    n, nnz = len(rp) - 1, len(ci)
+    d_rp = torch.from_numpy(rp).cuda()
+    d_ci = torch.from_numpy(ci).cuda()
+    g = sgc.Graph.from_device(n, nnz, d_rp.data_ptr(), d_ci.data_ptr())
+    base = 1000 * (rank + 1)
+    main = serve_stream(sgc, g, args.queries, args.rate, base)
+    sweep = []
+    if args.sweep:
+        for i, r in enumerate(float(x) for x in args.sweep.split(",")):
+            sweep.append(serve_stream(sgc, g, args.sweep_queries, r, base + 7919 * (i + 1), warm=False))
+    span = main["span_s"]
+    value = main["colorings"] / span
+    res = {"metric": METRIC, "value": value * world, "unit": "colorings/s", "n_gpus": world, "steps": args.queries,
+           "warmup": 12, "ms_per_step": 1e3 * span / args.queries, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "serving", "graph": "R-MAT scale 21, edge factor 16, a=.57 b=.19 c=.19, seed 1",
                       "templates": "Pruefer trees, 3..14 vertices (uniform)", "colorings_per_query": "uniform 1..32",
                       "arrivals": f"Poisson, {args.rate:g} queries/s", "budget_bytes": 120 << 30, "max_inflight": 8,
-                      "queries": Q, "parallelism": f"one server per GPU ({world})"},
-           "serving": {"offered_qps": args.rate, "achieved_qps": Q / span, "latency_p50_ms": float(np.percentile(lat, 50)),
-                       "latency_p99_ms": float(np.percentile(lat, 99)), "server_p50_ms": st["latency_p50_ms"],
-                       "server_p99_ms": st["latency_p99_ms"], "queue_p50_ms": st["queue_p50_ms"],
-                       "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"], "colorings": colorings,
-                       "span_s": span},
-           "gpu_launches": st["kernel_launches"]}
+                      "queries": args.queries, "parallelism": f"one server per GPU ({world})"},
+           "serving": main, "gpu_launches": main["kernel_launches"]}
+    if sweep:
+        ok = [x["offered_qps"] for x in sweep if x["achieved_qps"] >= 0.9 * x["offered_qps"]]
+        res["sweep"] = sweep
+        res["sustainable_qps"] = max(ok) if ok else None
+        res["capacity_qps"] = max(x["achieved_qps"] for x in sweep)
     if rank == 0:
         print(json.dumps(res), flush=True)
 
 
 def run_ablation(args, wl, rank, world, local):
-    """Pruned (SpMM + eMA) against unpruned (Algorithm 1 order) on the same colorings: the speed-up of
-    the pruning of Eq. 2 on the GPU (the paper reports it on CPUs against FASCIA)."""
+    """The paper's three variants on the GPU, same colorings (Section 6.1 and 7.1-7.2): Algorithm 1's loop
+    order with no pruning (FASCIA order), the pruned neighbour sums of Eq. 2 taken one column at a time
+    (PFASCIA: pruning without the row-wise SpMM), and the SpMM + eMA path (PGBSC).  pruning_speedup =
+    PFASCIA / FASCIA, vectorization_speedup = PGBSC / PFASCIA."""
     import torch
     import paper_1903_04395_gb300 as sgc
     torch.cuda.set_device(local)
@@ -462,31 +492,33 @@ def run_ablation(args, wl, rank, world, local):
     rp, ci = make_graph(wl)
     g = sgc.Graph(rp, ci)
     B, K, W = wl["batch"], args.steps, args.warmup
+    modes = (("pgbsc", 0), ("pfascia", 2), ("fascia", 1))
     out = []
     for name, spec in wl["templates"]:
         t = sgc.Template(make_parent(spec))
         row = {"template": name}
-        for mode in ("pruned", "unpruned"):
-            opt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream,
-                                       unpruned=1 if mode == "unpruned" else 0)
+        for mode, code in modes:
+            opt = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream, unpruned=code)
             seeds = np.arange(1, 1 + B * (W + K), dtype=np.uint64)
-            for s in range(W):
-                sgc.sgc_count(g.handle, t.handle, seeds[s * B:(s + 1) * B], opt)
+            for s_ in range(W):
+                sgc.sgc_count(g.handle, t.handle, seeds[s_ * B:(s_ + 1) * B], opt)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             maps = []
             e0.record(stream)
-            for s in range(W, W + K):
-                maps.append(sgc.sgc_count(g.handle, t.handle, seeds[s * B:(s + 1) * B], opt)[1].copy())
+            for s_ in range(W, W + K):
+                maps.append(sgc.sgc_count(g.handle, t.handle, seeds[s_ * B:(s_ + 1) * B], opt)[1].copy())
             e1.record(stream)
             torch.cuda.synchronize()
             row[mode] = {"colorings_per_s": K * B / (e0.elapsed_time(e1) / 1e3), "maps_first": float(maps[0][0])}
-        row["speedup"] = row["pruned"]["colorings_per_s"] / row["unpruned"]["colorings_per_s"]
-        row["same_counts"] = abs(row["pruned"]["maps_first"] - row["unpruned"]["maps_first"]) <= \
-            1e-5 * abs(row["pruned"]["maps_first"])
+        row["pruning_speedup"] = row["pfascia"]["colorings_per_s"] / row["fascia"]["colorings_per_s"]
+        row["vectorization_speedup"] = row["pgbsc"]["colorings_per_s"] / row["pfascia"]["colorings_per_s"]
+        row["total_speedup"] = row["pgbsc"]["colorings_per_s"] / row["fascia"]["colorings_per_s"]
+        first = row["pgbsc"]["maps_first"]
+        row["same_counts"] = all(abs(row[m]["maps_first"] - first) <= 1e-5 * abs(first) for m, _ in modes)
         out.append(row)
-    res = {"metric": METRIC, "value": out[0]["pruned"]["colorings_per_s"], "unit": "colorings/s", "n_gpus": world,
-           "steps": K, "warmup": W, "ms_per_step": 1e3 * B / out[0]["pruned"]["colorings_per_s"],
+    res = {"metric": METRIC, "value": out[0]["pgbsc"]["colorings_per_s"], "unit": "colorings/s", "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": 1e3 * B / out[0]["pgbsc"]["colorings_per_s"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "ablation", "graph": "R-MAT scale %d, edge factor 16, a=.57 b=.19 c=.19, seed 1"
                       % wl["scale"], "colorings_per_step": B},
@@ -737,7 +769,8 @@ def main():
     templates = [(name, sgc.Template(make_parent(spec))) for name, spec in wl["templates"]]
     NT = len(templates)
     K, W = args.steps, args.warmup
-    total_steps = W + K
+    # warm-up, timed steps, then steps of their own for per-template rates, the profiled pass and FP64
+    total_steps = W + K + max(2, K // 4) + 2 + 1 + max(2, K // 6)
     # distinct seeds for every (rank, step, template, coloring): each rank counts its own contiguous range
     from paper_1903_04395_gb300 import shard
     seeds = torch.from_numpy(shard.rank_seeds(1, world * total_steps * NT * B, rank, world).astype(np.int64)).cuda()
@@ -782,9 +815,9 @@ def main():
             ms = shard.max_over_ranks(ms)
         return ms, g.stats()["kernel_launches"] - l0, (sampler.summary() if sampler else None)
 
-    tune = 0 if (args.no_autotune or args.spmm_shape) else 1
+    tune = 0 if (args.no_autotune or args.spmm_shape or args.ema_rows) else 1
     opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream,
-                                 spmm_shape=args.spmm_shape, autotune=tune)
+                                 spmm_shape=args.spmm_shape, ema_rows=args.ema_rows, autotune=tune)
     t_w = time.perf_counter()
     run_steps(opt32, 0, W)  # warm-up: plans, autotuning (first call per template), CUDA-graph recording
     torch.cuda.synchronize()
@@ -865,6 +898,12 @@ def main():
     res["spmm_ema_gbs"] = se_bytes / (se_ms * 1e-3) / 1e9 if se_ms else None
     res["spmm_ema_frac"] = res["spmm_ema_gbs"] / peak if se_ms else None
     res["ops"] = [{k_: (round(v, 4) if isinstance(v, float) else v) for k_, v in o.items()} for o in ops]
+    # bytes an op actually has to move cannot stream faster than the copy peak: an op above it counts
+    # bytes its kernels do not move
+    above = [o["op"] for o in ops if o["compulsory_gbs"] > 1.05 * peak]
+    res["ops_compulsory_above_peak"] = above
+    if above:
+        print(f"warning: compulsory bytes above the copy peak for {above}", file=sys.stderr)
 
     if not args.no_fp64 and wl.get("fp64", True):
         opt64 = sgc.sgc_options_init(precision=sgc.SGC_FP64, batch=B, stream=stream.cuda_stream)

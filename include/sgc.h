@@ -93,21 +93,27 @@ typedef struct sgc_options {
                           neighbour and eight entries, any width), 10 bucketed specialised for the
                           batch, 16 grouped (1, 2 or 4 colorings per pass: a warp per row and
                           coloring sums the rows of each neighbour color in registers and adds each
-                          color's sum into the output row once); ops it does not fit keep
+                          color's sum into the output row once; columns in chunks of up to 512),
+                          17 grouped in chunks of up to 256 columns; ops it does not fit keep
                           theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
                           1 / 2 rows per lane (4..32 colorings per pass), or 103 = every operand in
                           registers (FP32; the shapes compiled in: 10 colors with a 3-color passive
-                          child and a 3-color active one, the default where it applies); ops it
-                          does not fit keep theirs; 0 (default) = planner or autotuner */
+                          child and a 3-color active one, the default where it applies), or 104 =
+                          scheduled (one coloring per pass: 8 rows staged by bulk copies, each
+                          output's split terms in rounds that read distinct shared-memory banks);
+                          ops it does not fit keep theirs; 0 (default) = planner or autotuner */
   int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
                           |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have
                           distinct colors; the estimate divides by k! / ((k - |T|)! k^|T|). */
-  int32_t unpruned;    /* 1 = ablation of the pruning (Eq. 2, Section 4.2): every combine in
-                          Algorithm 1's loop order, the neighbour sum taken again for each color
-                          set and split (no SpMM); same results, far more work.  0 (default). */
+  int32_t unpruned;    /* ablations, same results: 1 = without the pruning (Eq. 2, Section 4.2):
+                          every combine in Algorithm 1's loop order, the neighbour sum taken again
+                          for each color set and split (no SpMM); 2 = pruned as in Section 4.2
+                          (each neighbour sum once per passive color set) but one column at a time,
+                          a thread per vertex and column walking its neighbours, instead of the
+                          row-wise SpMM of Section 4.5.  0 (default) = pruned, SpMM + eMA. */
 } sgc_options;
 
 /* Fill *opt with the defaults described above. */
@@ -255,7 +261,7 @@ typedef struct sgc_tune_entry {
   int32_t shapes[8];         /* SpMM: 1 direct, 2 direct with prefetch, 3 bucketed, 4 register buckets,
                                 5 direct with packed positions, 6 / 7 direct with a copy ring,
                                 8 / 9 / 11 / 12 / 13 / 14 / 15 direct specialised for the batch, 10
-                                bucketed specialised, 16 grouped;
+                                bucketed specialised, 16 / 17 grouped;
                                 eMA: rows staged per block, or 101 / 102 vertex tiles */
   double ms[8];              /* device time of the op, one pass, per shape */
 } sgc_tune_entry;

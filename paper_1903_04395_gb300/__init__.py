@@ -254,7 +254,7 @@ SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buc
                7: "direct+ring4", 8: "direct-batch",
                9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12",
                13: "direct-batch-private", 14: "direct-batch-unrolled", 15: "direct-batch-wide",
-               16: "grouped"}
+               16: "grouped", 17: "grouped-256"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:
@@ -468,11 +468,13 @@ def _precision(name: str) -> int:
 
 def count(graph: Graph, template: Template, seeds, precision: str = "fp32", batch: int = 0, root: int = -1,
           mem_limit: int = 0, use_graph: bool = True, autotune: bool = False, spmm_shape: int = 0,
-          ema_rows: int = 0, colors: int = 0, unpruned: bool = False) -> CountResult:
+          ema_rows: int = 0, colors: int = 0, unpruned: int = 0) -> CountResult:
+    """unpruned: 0 = the SpMM + eMA path; 1 = Algorithm 1's loop order (no pruning); 2 = pruned neighbour
+    sums taken one column at a time (no row-wise SpMM).  True counts as 1."""
     opt = sgc_options_init(precision=_precision(precision), batch=batch, root=root,
                            mem_limit=mem_limit, use_graph=1 if use_graph else 0, autotune=1 if autotune else 0,
                            spmm_shape=spmm_shape, ema_rows=ema_rows, colors=colors,
-                           unpruned=1 if unpruned else 0)
+                           unpruned=int(unpruned))
     est, maps = sgc_count(graph.handle, template.handle, seeds, opt)
     return CountResult(est, maps)
 

@@ -154,7 +154,7 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
                           "/" + std::to_string(bmax) + (o.autotune ? "/tuned" : "") + "/s" +
                           std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows) + "/c" +
-                          std::to_string(o.colors) + (o.unpruned ? "/unpruned" : "");
+                          std::to_string(o.colors) + (o.unpruned ? "/unpruned" + std::to_string(o.unpruned) : "");
   for (auto& kv : g->plan_cache)
     if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
       *out = kv.second;
@@ -170,12 +170,12 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     return sh;
   };
   Plan p1;
-  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1, nullptr, o.colors, o.unpruned != 0);
+  sgc_status rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &p1, nullptr, o.colors, o.unpruned);
   if (rc != SGC_OK) return rc;
   if (forced) {
     const std::vector<int> sh = forced_shapes(p1);
     if ((rc = make_plan(g, t, o.precision, p1.root, p1.policy, 1, true, &p1, &sh,
-                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+                        o.colors, o.unpruned)) != SGC_OK) return rc;
   }
   if (p1.ws_bytes > mem_limit)
     return fail(SGC_ERR_OOM, "one coloring needs " + std::to_string(p1.ws_bytes) +
@@ -193,12 +193,12 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   set->bfit = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
-    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors, o.unpruned != 0);
+    rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors, o.unpruned);
     if (rc != SGC_OK) return rc;
     if (forced) {
       const std::vector<int> sh = forced_shapes(pb);
       if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, &sh,
-                          o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+                          o.colors, o.unpruned)) != SGC_OK) return rc;
     }
     if (pb.ws_bytes > mem_limit) break;
     set->by_batch[b] = std::move(pb);
@@ -302,7 +302,7 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
         if (!cands[i].empty()) shapes[i] = cands[i][std::min(c, cands[i].size() - 1)];
       Plan p;
       sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &p, &shapes,
-                                o.colors, o.unpruned != 0);
+                                o.colors, o.unpruned);
       if (rc != SGC_OK) return rc;
       TimedPass tp;
       if ((rc = time_pass(g, p, pool, st, &tp)) != SGC_OK) return rc;
@@ -343,7 +343,7 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
     }
     Plan tuned;
     sgc_status rc = make_plan(g, t, o.precision, base.root, base.policy, b, true, &tuned, &best,
-                              o.colors, o.unpruned != 0);
+                              o.colors, o.unpruned);
     if (rc != SGC_OK) return rc;
     set->by_batch[b] = std::move(tuned);
     const double per = pass_ms / b;
@@ -494,12 +494,13 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
       return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   }
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmGrouped)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0.." + std::to_string(kShapeSpmmGrouped));
+  if (o.unpruned < 0 || o.unpruned > 2) return fail(SGC_ERR_INVALID, "options.unpruned must be 0, 1 or 2");
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmGrouped8)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0.." + std::to_string(kShapeSpmmGrouped8));
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != 2 && o.ema_rows != 1 && o.ema_rows != kShapeEmaVertex1 &&
-      o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg)
-    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101, 102 or 103");
+      o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg && o.ema_rows != kShapeEmaSched)
+    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101, 102, 103 or 104");
   SGC_CUDA_TRY(cudaSetDevice(g->device));
   std::lock_guard<std::mutex> lock(g->mu);
   DevicePool& pool = device_pool(g->device);
@@ -790,7 +791,7 @@ sgc_status sgc_plan_get(const sgc_graph* g, const sgc_template* t, const sgc_opt
   Plan p;
   const int b = pow2_floor(std::max(1, std::min(32, o.batch > 0 ? o.batch : 1)));
   if ((rc = make_plan(g, t, o.precision, o.root, -1, b, false, &p, nullptr,
-                      o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+                      o.colors, o.unpruned)) != SGC_OK) return rc;
   out->root = p.root;
   out->n_tables = p.n_tables;
   out->n_spmm = p.n_spmm;

@@ -1179,6 +1179,46 @@ __global__ void k_spmm_reduce(const int32_t* __restrict__ heavy_seg, int32_t n_h
   if (std::is_same<T, float>::value) publish_max(st_out, m);
 }
 
+// The pruned neighbour sums one passive column at a time (the ablation of the
+// SpMM's row-wise vectorisation): P(v, S) for one column S, then the next -
+// a thread per (column S, row r = (v, coloring)), columns outermost, walks v's
+// whole neighbour list and adds the one entry of each neighbour's row that
+// holds S (index npos[c_v][S][c_u], ~0 when c_u is not in S).  Every P entry is
+// computed once, as in the pruned method, but each neighbour visit reads a
+// single entry instead of the neighbour's row.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_spmm_col(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t n_act,
+    const uint8_t* __restrict__ colors, int lb, int k, const T* __restrict__ Mp, int64_t ldp, T* __restrict__ P,
+    int64_t ld_out, int w_out, const uint32_t* __restrict__ npos, const ScaleState* st_in, ScaleState* st_out) {
+  const int64_t rows = (int64_t)n_act << lb;
+  const int64_t items = rows * ld_out;
+  const int batch = 1 << lb;
+  float m = 0.f;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int S = (int)(it / rows);
+    const int64_t r = it - (int64_t)S * rows;
+    const int64_t v = r >> lb;
+    const int b = (int)(r & (batch - 1));
+    T sum = T(0);
+    if (S < w_out) {
+      const uint32_t* np = npos + ((int64_t)colors[r] * w_out + S) * k;
+      for (int32_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q) {
+        const int32_t u = __ldg(col_idx + q);
+        const uint32_t pj = __ldg(np + colors[(int64_t)u * batch + b]);
+        if (pj != 0xFFFFFFFFu) sum += __ldg(Mp + (((int64_t)u * ldp + pj) << lb) + b);
+      }
+    }
+    P[((v * ld_out + S) << lb) + b] = sum;
+    m = fmaxf(m, (float)sum);
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+  }
+}
+
 // ---------------------------------------------- neighbours grouped by color --
 // For the grouped SpMM form, per coloring b: the neighbours u of a row (or a
 // heavy-row segment) whose color differs from the row's, grouped by color in
@@ -1306,21 +1346,33 @@ __global__ void __launch_bounds__(kBlock) k_spmm_g(
         __syncwarp();
       };
       int cur = -1;
+      // neighbour t's row entries are loaded while neighbour t - 1's are added (and a finished
+      // group's sum is added into the output row), so two neighbours' loads are in flight
+      auto load = [&](int32_t u, T (&x)[NR]) {
+        const T* src = Min + ((int64_t)u * ld_in + jl) * B + b;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) x[r] = jl + 32 * r < w_in ? __ldg(src + 32 * r * B) : T(0);
+      };
       for (int e0 = 0; e0 < kept; e0 += 32) {
         const int cnt = min(32, kept - e0);
         const int32_t u_lane = lane < cnt ? __ldg(ids + e0 + lane) : 0;
         const int c_lane = lane < cnt ? (int)__ldg(cs + e0 + lane) : 0;
+        T x[NR];
+        load(__shfl_sync(0xffffffffu, u_lane, 0), x);
         for (int t = 0; t < cnt; ++t) {
-          const int32_t u = __shfl_sync(0xffffffffu, u_lane, t);
           const int c = __shfl_sync(0xffffffffu, c_lane, t);
+          const int32_t un = __shfl_sync(0xffffffffu, u_lane, t + 1 < cnt ? t + 1 : t);
+          T xn[NR];
+          if (t + 1 < cnt) load(un, xn);
           if (c != cur) {
             if (cur >= 0) flush(cur);
             cur = c;
           }
-          const T* src = Min + ((int64_t)u * ld_in + jl) * B + b;
 #pragma unroll
-          for (int r = 0; r < NR; ++r)
-            if (jl + 32 * r < w_in) a[r] += __ldg(src + 32 * r * B);
+          for (int r = 0; r < NR; ++r) {
+            a[r] += x[r];
+            x[r] = xn[r];
+          }
         }
       }
       if (cur >= 0) flush(cur);
@@ -1431,6 +1483,193 @@ __global__ void __launch_bounds__(kBlock) k_ema(
         if (r + 32 * q < nr) out[(((rq >> lb) * ldt + S) << lb) + (rq & bmask)] = v;
         m = fmaxf(m, (float)v);
       }
+    }
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_a->e + st_p->e + s;
+  }
+}
+
+// ---- bulk copies (TMA, one-dimensional) into this CTA's shared memory, completed on an mbarrier --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// wait for phase `parity` of the barrier, at most `limit` polls; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// eMA with a bank-conflict-free schedule (one coloring per pass).  A block
+// stages R consecutive rows, each [M_a row | P row | 4 zero words] (the passive
+// row starts `pofs` words in; a table combined with itself is staged once), by bulk
+// copies completed on an mbarrier.  Outputs go in groups of 32, lane l of a
+// group computing output 32 g + l for all R rows: the table orders each
+// group's split terms in rounds in which the 32 lanes read 32 distinct banks
+// of the active columns and 32 distinct banks of the passive ones (all lanes
+// read the same row at a time), so each term costs two conflict-free shared
+// loads for R multiply-adds, and a table word serves R rows.  Work units are
+// (group, share of its rounds); with fewer groups than warps a group's rounds
+// are split and the shares' partial sums added in share order, so results
+// are deterministic.  A wait on the copies that runs out of polls writes NaN
+// to the tile's outputs (which reaches the colorful maps) instead of hanging.
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * kEmaSchedWarps) k_ema_s(
+    const T* __restrict__ Ma, int64_t lda, const T* __restrict__ P, int64_t ldp, T* __restrict__ out, int64_t ldt,
+    const uint32_t* __restrict__ tab, int G, int upg, int sym, int pofs, int rw, int64_t nv, int nsplit,
+    const ScaleState* st_a, const ScaleState* st_p, ScaleState* st_out) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  T* rows = reinterpret_cast<T*>(sm_raw);
+  T* part = rows + (int64_t)R * rw;                               // upg > 1: [unit][row][lane]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(part + (upg > 1 ? (int64_t)G * upg * 32 * R : 0));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  float scale = sym ? 2.f : 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    const float bound = (float)(sym ? 2 * nsplit : nsplit) * state_max(st_a) * state_max(st_p);
+    s = shift_for(bound);
+    scale *= pow2f(-s);
+  }
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  // every row ends in 4 zero words, which idle slots of the schedule read (no copy writes them)
+  const int zofs = rw - 4;
+  for (int i = threadIdx.x; i < 4 * R; i += blockDim.x) rows[(int64_t)(i >> 2) * rw + zofs + (i & 3)] = T(0);
+  const uint32_t idle_e = (uint32_t)zofs | (uint32_t)(zofs - pofs) << 16;
+  __syncthreads();
+  const int nunits = G * upg;
+  const uint32_t row_a = (uint32_t)(lda * (int64_t)sizeof(T)), row_p = (uint32_t)(ldp * (int64_t)sizeof(T));
+  uint32_t parity = 0;
+  float m = 0.f;
+  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < nv; r0 += (int64_t)gridDim.x * R) {
+    const int nr = (int)(nv - r0 < R ? nv - r0 : R);
+    __syncthreads();  // every read of the previous tile is done
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect_tx(bar, (uint32_t)nr * (row_a + (sym ? 0u : row_p)));
+      for (int r = 0; r < nr; ++r) {
+        bulk_g2s(rows + (int64_t)r * rw, Ma + (r0 + r) * lda, row_a, bar);
+        if (!sym) bulk_g2s(rows + (int64_t)r * rw + pofs, P + (r0 + r) * ldp, row_p, bar);
+      }
+    }
+    const bool late = !mbar_wait(bar, parity, 1u << 24);
+    parity ^= 1u;
+    if (__syncthreads_or(late)) {  // the copies did not complete: poison this tile's outputs, all threads stop
+      for (int64_t i = threadIdx.x; i < (int64_t)nr * ldt; i += blockDim.x)
+        out[(r0 + i / ldt) * ldt + i % ldt] = T(NAN);
+      return;
+    }
+    for (int u = warp; u < nunits; u += nwarps) {
+      const int g = u / upg, share = u - g * upg;
+      const uint32_t first = __ldg(tab + 2 * g), nrounds = __ldg(tab + 2 * g + 1);
+      const uint32_t j0 = (uint32_t)(((uint64_t)nrounds * share) / upg);
+      const uint32_t j1 = (uint32_t)(((uint64_t)nrounds * (share + 1)) / upg);
+      const uint32_t* tp = tab + (int64_t)first * 32 + lane;
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      // eight rounds' table words are loaded before they are used (the table streams from L2)
+      for (uint32_t j = j0; j < j1; j += 8) {
+        uint32_t ev[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ev[q] = j + q < j1 ? __ldg(tp + (int64_t)(j + q) * 32) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t e = ev[q] == 0xFFFFFFFFu ? idle_e : ev[q];  // idle: the zero word (no branch)
+          const T* pa = rows + (e & 0xFFFFu);
+          const T* pp = rows + pofs + (e >> 16);
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] += pa[(int64_t)r * rw] * pp[(int64_t)r * rw];
+        }
+      }
+      const int S = g * 32 + lane;
+      if (upg == 1) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < nr && S < ldt) {
+            const T v = acc[r] * (T)scale;
+            out[(r0 + r) * ldt + S] = v;
+            m = fmaxf(m, (float)v);
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) part[((int64_t)u * R + r) * 32 + lane] = acc[r];
+      }
+    }
+    if (upg > 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < G * 32 * R; i += blockDim.x) {
+        const int g = i / (32 * R), r = (i / 32) % R, l = i % 32, S = g * 32 + l;
+        if (r >= nr || S >= ldt) continue;
+        T acc = T(0);
+        for (int sh = 0; sh < upg; ++sh) acc += part[((int64_t)(g * upg + sh) * R + r) * 32 + l];
+        const T v = acc * (T)scale;
+        out[(r0 + r) * ldt + S] = v;
+        m = fmaxf(m, (float)v);
+      }
+    }
+  }
+  if (std::is_same<T, float>::value) {
+    publish_max(st_out, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_a->e + st_p->e + s;
+  }
+}
+
+// eMA for rows too wide to stage in shared memory (17 and 18 colors): one
+// warp per row, lanes over the output columns, both operands read through L1
+// at the raw split indices (I(A), I(S \ A)) of the table's [j][S] layout.
+// Same sums, in the same order, as k_ema.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_ema_gl(
+    const T* __restrict__ Ma, int64_t lda, const T* __restrict__ P, int64_t ldp, T* __restrict__ out, int64_t ldt,
+    int ct, const uint2* __restrict__ tab, int nsplit, int sym, int64_t rows, int lb, const ScaleState* st_a,
+    const ScaleState* st_p, ScaleState* st_out) {
+  const int64_t bmask = (1 << lb) - 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  float scale = sym ? 2.f : 1.f;
+  int s = 0;
+  if (std::is_same<T, float>::value) {
+    const float bound = (float)(sym ? 2 * nsplit : nsplit) * state_max(st_a) * state_max(st_p);
+    s = shift_for(bound);
+    scale *= pow2f(-s);
+  }
+  float m = 0.f;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+    const T* a = Ma + (((r >> lb) * lda) << lb) + (r & bmask);
+    const T* p = P + (((r >> lb) * ldp) << lb) + (r & bmask);
+    T* o = out + (((r >> lb) * ldt) << lb) + (r & bmask);
+    for (int S = lane; S < ldt; S += 32) {
+      T acc = T(0);
+      if (S < ct)
+        for (int j = 0; j < nsplit; ++j) {
+          const uint2 e = __ldg(tab + (int64_t)j * ct + S);
+          acc += __ldg(a + ((int64_t)e.x << lb)) * __ldg(p + ((int64_t)e.y << lb));
+        }
+      const T v = S < ct ? acc * (T)scale : T(0);
+      o[(int64_t)S << lb] = v;
+      m = fmaxf(m, (float)v);
     }
   }
   if (std::is_same<T, float>::value) {
@@ -2269,9 +2508,40 @@ sgc_status launch_ema_reg(const PlanOp& op, const float* Ma, const float* P, flo
   return fail(SGC_ERR_INTERNAL, "eMA register form not compiled in for this shape");
 }
 
+template <typename T, int R>
+sgc_status launch_ema_s(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t nv,
+                        const ScaleState* sa, const ScaleState* sp, ScaleState* so, size_t smem_cap, cudaStream_t st) {
+  const int elem = (int)sizeof(T);
+  const size_t smem = (size_t)ema_sched_smem(R, op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, op.ema_upg);
+  if (smem > smem_cap) return fail(SGC_ERR_UNSUPPORTED, "scheduled eMA rows do not fit in shared memory");
+  allow_smem(k_ema_s<T, R>, smem);
+  int dev = 0, nsm = 0, nb = 0;
+  SGC_CUDA_TRY(cudaGetDevice(&dev));
+  SGC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ema_s<T, R>, 32 * kEmaSchedWarps, smem) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  const int64_t tiles = (nv + R - 1) / R;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)nb * nsm);
+  const int G = (int)((op.cols_out + 31) / 32);
+  const int rw = (int)ema_sched_rw(op.ld_a, op.ld_p, op.ema_sym);
+  k_ema_s<T, R><<<std::max(grid, 1), 32 * kEmaSchedWarps, smem, st>>>(Ma, op.ld_a, P, op.ld_p, out, op.ld_out, tab, G, op.ema_upg,
+                                                         op.ema_sym ? 1 : 0, op.ema_sym ? 0 : (int)op.ld_a, rw, nv,
+                                                         (int)op.nsplit, sa, sp, so);
+  return SGC_OK;
+}
+
 template <typename T>
 sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const uint32_t* tab, int64_t rows, int lb,
                       const ScaleState* sa, const ScaleState* sp, ScaleState* so, size_t smem_cap, cudaStream_t st) {
+  if (op.ema_sched > 0) {
+    if (lb != 0) return fail(SGC_ERR_INTERNAL, "the scheduled eMA takes one coloring per pass");
+    switch (op.ema_sched) {
+      case 8: return launch_ema_s<T, 8>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
+      case 4: return launch_ema_s<T, 4>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
+      default: return launch_ema_s<T, 2>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
+    }
+  }
   if (op.ema_reg_k > 0) {
     if constexpr (std::is_same<T, float>::value)
       return launch_ema_reg(op, Ma, P, out, rows >> lb, lb, sa, sp, so, st);
@@ -2301,7 +2571,11 @@ sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const u
     case 4: launch_ema_r<T, 4, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
     case 2: launch_ema_r<T, 2, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
     case 1: launch_ema_r<T, 1, 1>(op, Ma, P, out, tab, rows, lb, sa, sp, so, st); break;
-    default: return fail(SGC_ERR_UNSUPPORTED, "eMA row does not fit in shared memory");
+    default:  // rows too wide to stage: operands through L1 (the table holds raw indices)
+      k_ema_gl<T><<<grid_for(rows, kBlock / 32, 1 << 30), kBlock, 0, st>>>(
+          Ma, op.ld_a, P, op.ld_p, out, op.ld_out, (int)op.cols_out, reinterpret_cast<const uint2*>(tab),
+          (int)op.nsplit, op.ema_sym ? 1 : 0, rows, lb, sa, sp, so);
+      break;
   }
   return SGC_OK;
 }
@@ -2328,8 +2602,10 @@ int profile_slot(Profiler* prof, const PlanOp& op, int batch, int k) {
 
 // The grouped SpMM: the color-grouped neighbour lists of the pass (built by the
 // first grouped op), then a warp per (item, coloring) with the chunk width
-// 32 * NR closest above the row width (at most 1024 columns per chunk), then
-// the heavy rows' segment partials summed.
+// 32 * NR closest above the row width (at most 512 columns per chunk, or 256 for
+// op.spmm_variant == 15: fewer registers, more warps), then
+// the heavy rows' segment partials summed.  Chunks of at most 512 columns keep two neighbours'
+// rows and the sums in registers at 4 warps of 8 per SM's register file.
 template <typename T>
 sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanOp& op, int batch,
                                const uint8_t* colors, const T* M, T* P, T* scratch, const uint32_t* tab,
@@ -2361,7 +2637,8 @@ sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanO
   const size_t smem = per_warp * w;
   const int w_in = (int)op.cols_p;
   const int need = (w_in + 31) / 32;
-  const int nr = need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : 32;
+  const int nr_cap = op.spmm_variant == 15 ? 8 : 16;  // wider rows: chunks of 32 * nr_cap columns
+  const int nr = std::min(nr_cap, need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16);
   const uint16_t* tab16 = reinterpret_cast<const uint16_t*>(tab);
   const unsigned grid = (unsigned)grid_for(nitems * batch, w, 1 << 30);
 #define SGC_G(B_, NR_)                                                                                          \
@@ -2378,8 +2655,7 @@ sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanO
       case 2: SGC_G(B_, 2); break;      \
       case 4: SGC_G(B_, 4); break;      \
       case 8: SGC_G(B_, 8); break;      \
-      case 16: SGC_G(B_, 16); break;    \
-      default: SGC_G(B_, 32); break;    \
+      default: SGC_G(B_, 16); break;    \
     }                                   \
   } while (0)
   if (batch == 1) SGC_G2(1);
@@ -2480,7 +2756,16 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
         break;
       }
       case OP_SPMM: {
-        if (op.spmm_variant == 13) {
+        if (op.spmm_variant == 14) {
+          const int64_t items = rows * op.ld_out;
+          k_spmm_col<T><<<grid_for(items, kBlock, 64 * num_sms), kBlock, 0, st>>>(
+              g->d_row_ptr, g->d_col_idx, g->n_act, colors, lb, plan.k, reinterpret_cast<const T*>(buf(op.in_p)),
+              op.ld_p, reinterpret_cast<T*>(buf(op.out)), op.ld_out, (int)op.cols_out, d_tabs + op.tab_off,
+              S(op.state_p), S(op.state_out));
+          ++nk;
+          break;
+        }
+        if (op.spmm_variant == 13 || op.spmm_variant == 15) {
           sgc_status rc = launch_spmm_grouped<T>(g, plan, op, B, colors, reinterpret_cast<const T*>(buf(op.in_p)),
                                                  reinterpret_cast<T*>(buf(op.out)), scratch, d_tabs + op.tab_off,
                                                  reinterpret_cast<int32_t*>(buf(plan.buf_gids)),

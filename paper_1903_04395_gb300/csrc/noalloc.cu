@@ -92,7 +92,7 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
   const int want = std::min(32, o.batch > 0 ? o.batch : (int)n_iter);
   while (bmax * 2 <= want) bmax *= 2;
   Plan top;
-  rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &top, nullptr, o.colors, o.unpruned != 0);
+  rc = make_plan(g, t, o.precision, o.root, -1, 1, true, &top, nullptr, o.colors, o.unpruned);
   if (rc != SGC_OK) return rc;
   if (static_need(top) > (int64_t)kStaticWorkspaceBytes)
     return fail(SGC_ERR_UNSUPPORTED, "this count needs " + std::to_string(static_need(top)) +
@@ -105,7 +105,7 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
     if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr,
-                        o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+                        o.colors, o.unpruned)) != SGC_OK) return rc;
     if (static_need(pb) > (int64_t)kStaticWorkspaceBytes) break;
     bfit = b;
   }
@@ -115,7 +115,7 @@ extern "C" sgc_status sgc_count_device_static(const sgc_graph* g, const sgc_temp
     Plan plan;
     for (;;) {
       if ((rc = make_plan(g, t, o.precision, root, policy, b, true, &plan, nullptr,
-                          o.colors, o.unpruned != 0)) != SGC_OK) return rc;
+                          o.colors, o.unpruned)) != SGC_OK) return rc;
       if (static_need(plan) <= (int64_t)kStaticWorkspaceBytes) break;
       if (b == 1) return fail(SGC_ERR_INTERNAL, "static workspace plan grew beyond its size");
       b /= 2;  // a smaller pass needs less

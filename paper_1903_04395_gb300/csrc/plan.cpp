@@ -284,8 +284,9 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
   auto it = cache->find(key);
   if (it != cache->end()) return it->second;
   const int K = k - 1;
-  // align each table to 4 words
-  while (tabs->size() % 4) tabs->push_back(0);
+  // align each table to 4 words (the scheduled eMA's to 32: its rounds are 128-byte lines)
+  const size_t align = (kind == OP_EMA + 300 || kind == OP_EMA + 400) ? 32 : 4;
+  while (tabs->size() % align) tabs->push_back(0);
   int64_t off = (int64_t)tabs->size();
   if (kind == OP_SPMM) {
     // [c_v][c_u][j]: a neighbour u of color c_u holds, at index j, the count for the
@@ -459,6 +460,75 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
       }
     }
     tabs->insert(tabs->end(), tab.begin(), tab.end());
+  } else if (kind == OP_EMA + 300 || kind == OP_EMA + 400) {
+    // scheduled eMA (k_ema_s, one coloring per pass): outputs in groups of 32 (lane = output), each
+    // group's split terms (I(A), I(S \ A)) ordered in rounds so that in every round the 32 lanes read
+    // active columns in 32 distinct shared-memory banks and passive columns in 32 distinct banks
+    // (the passive row starts `ema_rows` words after the active one: ema_rows carries that offset
+    // here; lanes reading the same word share its bank); an idle slot is all ones.  Layout: per group (round offset, rounds), then the rounds,
+    // 32 words each (I(A) | I(S \ A) << 16).  OP_EMA + 400: the symmetric form (each unordered split
+    // once).  Greedy: every round, lanes with the most terms left pick first, each its first term
+    // whose two banks are still free.
+    const bool sym = kind == OP_EMA + 400;
+    const int tt = t - 1, aa = a - 1;
+    const uint32_t pofs = (uint32_t)ema_rows;
+    const uint64_t ct = cr.nsets(tt);
+    const int64_t G = ((int64_t)ct + 31) / 32;
+    std::vector<std::vector<uint32_t>> lists(32);
+    std::vector<uint32_t> body;
+    std::vector<uint32_t> hdr(2 * (size_t)G);
+    for (int64_t gi = 0; gi < G; ++gi) {
+      size_t left = 0;
+      for (int l = 0; l < 32; ++l) {
+        lists[l].clear();
+        const uint64_t S = (uint64_t)gi * 32 + (uint64_t)l;
+        if (S >= ct) continue;
+        const uint32_t m = cr.unrank_mask(S, tt);
+        for (uint32_t sub = m;; sub = (sub - 1) & m) {
+          if (__builtin_popcount(sub) == aa) {
+            const uint32_t ia = cr.rank_mask(sub), ip = cr.rank_mask(m & ~sub);
+            if (!sym || ia < ip) lists[l].push_back(ia | ip << 16);
+          }
+          if (sub == 0) break;
+        }
+        left += lists[l].size();
+      }
+      hdr[2 * gi] = (uint32_t)(body.size() / 32);
+      uint32_t rounds = 0;
+      std::vector<int> order(32);
+      while (left > 0) {
+        for (int l = 0; l < 32; ++l) order[l] = l;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return lists[x].size() > lists[y].size(); });
+        // a bank taken by one word stays free for that same word (lanes reading one word broadcast)
+        uint32_t word_a[32], word_p[32];
+        for (int l = 0; l < 32; ++l) word_a[l] = word_p[l] = 0xFFFFFFFFu;
+        uint32_t slot[32];
+        for (int l = 0; l < 32; ++l) slot[l] = 0xFFFFFFFFu;
+        for (int l : order) {
+          auto& L = lists[l];
+          for (size_t i = 0; i < L.size(); ++i) {
+            const uint32_t wa = L[i] & 0xFFFFu, wp = pofs + (L[i] >> 16);
+            const uint32_t ba = wa & 31u, bp = wp & 31u;
+            if ((word_a[ba] != 0xFFFFFFFFu && word_a[ba] != wa) || (word_p[bp] != 0xFFFFFFFFu && word_p[bp] != wp))
+              continue;
+            word_a[ba] = wa;
+            word_p[bp] = wp;
+            slot[l] = L[i];
+            L.erase(L.begin() + (int64_t)i);
+            --left;
+            break;
+          }
+        }
+        body.insert(body.end(), slot, slot + 32);
+        ++rounds;
+      }
+      hdr[2 * gi + 1] = rounds;
+    }
+    tabs->insert(tabs->end(), hdr.begin(), hdr.end());
+    while ((tabs->size() - (size_t)off) % 32) tabs->push_back(0);  // rounds start on a 128-byte line
+    for (int64_t gi = 0; gi < G; ++gi) (*tabs)[(size_t)off + 2 * gi] += (uint32_t)((tabs->size() - (size_t)off) / 32);
+    tabs->insert(tabs->end(), body.begin(), body.end());
   } else if (kind == OP_FINAL) {
     // [I_p]: rank of the complement (among all K relative colors) of the p-subset I_p,
     // an (a-1)-subset: the active child's index for the full color set
@@ -516,6 +586,25 @@ static void use_buf(Plan* P, int buf, int op) {
   if (buf < 0) return;
   P->bufs[buf].first = std::min(P->bufs[buf].first, op);
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
+}
+
+int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg) {
+  const int64_t G = (ct + 31) / 32;
+  // fewer groups than warps: each group's rounds in W / gcd(G, W) shares, so that the G * shares
+  // units divide evenly among the W warps
+  const int64_t W = kEmaSchedWarps;
+  int64_t gcd = W, x = G % W;
+  for (int64_t y = W; x != 0;) {
+    const int64_t r = y % x;
+    y = x;
+    x = r;
+    gcd = y;
+  }
+  *upg = G < W ? (int)(W / gcd) : 1;
+  if (ema_sched_rw(ld_a, ld_p, sym) >= 65535) return 0;  // every word of a row has a 16-bit index
+  for (int r : {8, 4, 2})
+    if (ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= smem_cap) return r;
+  return 0;
 }
 
 static int64_t smem_cap_of(const sgc_graph* g) { return g->smem_optin > 0 ? g->smem_optin : 227 * 1024; }
@@ -662,7 +751,7 @@ static void plan_unpruned(const sgc_graph* g, const Builder& B, int k, int tk, i
 // evaluating the single full color set.
 static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy,
                      int batch, bool build_tabs, Plan* P, const std::vector<int>* shapes = nullptr,
-                     int colors = 0, bool unpruned = false) {
+                     int colors = 0, int unpruned = 0) {
   Rooted R;
   root_tree(t, root, &R);
   Builder B(R, policy);
@@ -699,7 +788,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   P->final_blocks = (4 * std::max(1, g->num_sms) + 31) / 32 * 32;  // multiple of 32: see k_final
   P->buf_partials = add_buf(P, "partials", 8LL * batch * P->final_blocks, 0);
 
-  if (unpruned) {
+  if (unpruned == 1) {
     plan_unpruned(g, B, k, tk, batch, build_tabs, P);
     P->buf_states = add_buf(P, "states", 8LL * std::max(1, P->n_states), 0);
     P->scratch_width = 0;
@@ -777,6 +866,12 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_buckets = false;
           op.spmm_variant = 11;
         }
+        if (batch == 1 && spmm_grouped_fits(batch, op.ld_out, elem, smem_cap_of(g)) && !std::getenv("SGC_SPMM_DIRECT")) {
+          // one coloring per pass: the grouped form, measured fastest or within 2% of the fastest on
+          // every SpMM of the 12-, 13- and 15-vertex trees on R-MAT 21 (narrow rows 1.4-3x faster)
+          op.spmm_buckets = false;
+          op.spmm_variant = op.cols_p <= 256 ? 13 : 15;
+        }
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
         if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
           op.spmm_buckets = true;
@@ -803,9 +898,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         } else if (shape == kShapeSpmmWide && op.ld_out < 65535) {
           op.spmm_buckets = false;
           op.spmm_variant = 12;
-        } else if (shape == kShapeSpmmGrouped && spmm_grouped_fits(batch, op.ld_out, elem, smem_cap_of(g))) {
+        } else if ((shape == kShapeSpmmGrouped || shape == kShapeSpmmGrouped8) &&
+                   spmm_grouped_fits(batch, op.ld_out, elem, smem_cap_of(g))) {
           op.spmm_buckets = false;
-          op.spmm_variant = 13;
+          op.spmm_variant = shape == kShapeSpmmGrouped ? 13 : 15;
         } else if (shape == kShapeSpmmUnrolled && spmm_unrolled_fits(batch, op.cols_p, op.ld_out)) {
           op.spmm_buckets = false;
           op.spmm_variant = 11;
@@ -823,7 +919,14 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_variant = 0;
           op.spmm_pos_bytes = op.ld_out < 255 ? 1 : 2;
         }
-        op.shape = op.spmm_variant == 13   ? kShapeSpmmGrouped
+        if (unpruned == 2) {  // the pruned sums one passive column at a time
+          op.spmm_buckets = false;
+          op.spmm_variant = 14;
+          op.spmm_pos_bytes = 0;
+        }
+        op.shape = op.spmm_variant == 14   ? 0
+                   : op.spmm_variant == 15 ? kShapeSpmmGrouped8
+                   : op.spmm_variant == 13 ? kShapeSpmmGrouped
                    : op.spmm_variant == 12 ? kShapeSpmmWide
                    : op.spmm_variant == 11 ? kShapeSpmmUnrolled
                    : op.spmm_variant == 10 ? kShapeSpmmDirectBPriv
@@ -846,7 +949,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                                                            &P->tabs, &tcache)
                      : op.spmm_variant == 12 ? build_table(cr, k, (OpKind)(OP_SPMM + 700), Pc.size, batch,
                                                            &P->tabs, &tcache)
-                     : op.spmm_variant == 13 ? build_table(cr, k, (OpKind)(OP_SPMM + 800), Pc.size, 0,
+                     : op.spmm_variant == 13 || op.spmm_variant == 15
+                                             ? build_table(cr, k, (OpKind)(OP_SPMM + 800), Pc.size, 0, &P->tabs,
+                                                           &tcache)
+                     : op.spmm_variant == 14 ? build_table(cr, k, (OpKind)(OP_SPMM + 500), Pc.size, 0,
                                                            &P->tabs, &tcache)
                      : op.spmm_buckets       ? build_table(cr, k, (OpKind)(OP_SPMM + 100), Pc.size, 0, &P->tabs,
                                                            &tcache)
@@ -933,12 +1039,29 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.ema_reg_k = K;
         op.ema_vrpl = 0;
       }
-      op.shape = op.ema_reg_k ? kShapeEmaReg : op.ema_vrpl ? 100 + op.ema_vrpl : op.ema_rows;
+      // the scheduled form (one coloring per pass) when forced or tuned, and by default for rows of
+      // 256 words or more (measured faster than every other form on every such combine of the 13-
+      // and 15-vertex trees on R-MAT 21; slower on rows of about a hundred words)
+      const bool sched_default = shape == 0 && op.ld_a + (op.ema_sym ? 0 : op.ld_p) >= 256;
+      if (!op.ema_reg_k && batch == 1 && (shape == kShapeEmaSched || sched_default)) {
+        int upg = 1;
+        const int r = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, smem_cap, &upg);
+        if (r > 0) {
+          op.ema_sched = r;
+          op.ema_upg = upg;
+          op.ema_vrpl = 0;
+        }
+      }
+      op.shape = op.ema_reg_k ? kShapeEmaReg : op.ema_sched ? kShapeEmaSched : op.ema_vrpl ? 100 + op.ema_vrpl
+                                                                                          : op.ema_rows;
       if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
       // the vertex-tile kernel takes the raw split indices (rows 0, no column offset)
-      op.tab_off = build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
+      op.tab_off = !build_tabs ? 0
+                   : op.ema_sched ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 400) : (OpKind)(OP_EMA + 300),
+                                                C.size, A.size, &P->tabs, &tcache, op.ema_sym ? 0 : (int)op.ld_a, 0)
+                   : build_tabs ? build_table(cr, k, op.ema_sym ? (OpKind)(OP_EMA + 200) : OP_EMA, C.size, A.size,
                                             &P->tabs, &tcache, op.ema_vrpl ? 0 : op.ema_rows,
-                                            op.ema_vrpl ? 0 : op.cols_a)
+                                            (op.ema_vrpl || op.ema_rows == 0) ? 0 : op.cols_a)
                               : 0;
       op.state_out = table_state[c] = n_states++;
       op.out = table_buf[c] = add_buf(P, "T" + std::to_string(c), rows * op.ld_out * elem, idx);
@@ -989,12 +1112,19 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         f.in_p == e.in_p && f.p == e.p && ema_final_compiled(e.ema_reg_k, e.p)) {
       e.ema_final = true;
       f.final_fused = true;
+      // the eMA's table is never stored: it takes no workspace, and the pair reads the passive
+      // table once (the final op only sums the block partials)
+      const double table_bytes = (double)elem * nv * (double)e.cols_out;
+      P->est_bytes -= table_bytes + (double)elem * nv * (double)(f.cols_a + f.cols_p);
+      P->bufs[e.out].bytes = 16;
+      e.alg_bytes = (double)elem * nv * batch * (double)e.cols_p;
+      f.alg_bytes = 8.0 * batch * (double)P->final_blocks;
     }
   }
   P->n_states = n_states;
   P->buf_states = add_buf(P, "states", 8LL * std::max(1, n_states), 0);
   bool grouped = false;
-  for (const PlanOp& op : P->ops) grouped |= op.kind == OP_SPMM && op.spmm_variant == 13;
+  for (const PlanOp& op : P->ops) grouped |= op.kind == OP_SPMM && (op.spmm_variant == 13 || op.spmm_variant == 15);
   if (grouped) {
     const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
     P->buf_gids = add_buf(P, "group_ids", 4LL * batch * g->nnz, 0);
@@ -1027,7 +1157,12 @@ static bool tables_in_range(const Plan& P, int k) {
       const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
       for (int64_t i = 0; i < n; ++i)
         if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
-    } else if (op.kind == OP_SPMM && op.spmm_variant == 13) {
+    } else if (op.kind == OP_SPMM && op.spmm_variant == 14) {
+      const int64_t n = (int64_t)k * op.cols_out * k;
+      if (n > left) return false;
+      for (int64_t i = 0; i < n; ++i)
+        if (t[i] != 0xFFFFFFFFu && t[i] >= (uint32_t)op.cols_p) return false;
+    } else if (op.kind == OP_SPMM && (op.spmm_variant == 13 || op.spmm_variant == 15)) {
       const int64_t n = (int64_t)k * k * op.cols_p;
       if ((n + 1) / 2 > left) return false;
       const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
@@ -1081,7 +1216,22 @@ static bool tables_in_range(const Plan& P, int k) {
       const int64_t wpt = op.in_p < 0 ? 1 : op.ld_p;  // entries of a passive row
       for (int64_t i = 0; i < n2; ++i)
         if (t2[i] != 0xFFFFFFFFu && (int64_t)t2[i] >= wpt) return false;
-    } else if (op.kind == OP_EMA && op.ema_vrpl > 0) {
+    } else if (op.kind == OP_EMA && op.ema_sched > 0) {
+      const int64_t G = (op.cols_out + 31) / 32;
+      if (2 * G > left) return false;
+      const uint32_t lim_p = (uint32_t)(op.ema_sym ? op.cols_a : op.cols_p);
+      int64_t terms = 0;
+      for (int64_t gi = 0; gi < G; ++gi) {
+        const int64_t first = t[2 * gi], n = t[2 * gi + 1];
+        if ((first + n) * 32 > left) return false;
+        for (int64_t i = first * 32; i < (first + n) * 32; ++i) {
+          if (t[i] == 0xFFFFFFFFu) continue;
+          if ((t[i] & 0xFFFFu) >= (uint32_t)op.cols_a || (t[i] >> 16) >= lim_p) return false;
+          ++terms;
+        }
+      }
+      if (terms != op.cols_out * op.nsplit) return false;  // every split term scheduled exactly once
+    } else if (op.kind == OP_EMA && op.ema_reg_k == 0 && (op.ema_vrpl > 0 || op.ema_rows == 0)) {
       const int64_t n = 2 * op.cols_out * op.nsplit;
       if (n > left) return false;
       for (int64_t i = 0; i < n; i += 2)
@@ -1106,7 +1256,10 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
   const PlanOp& op = P.ops[i];
   const int smem_cap = g->smem_optin > 0 ? g->smem_optin : 227 * 1024;
   if (op.kind == OP_SPMM) {
-    if (spmm_grouped_fits(P.batch, op.ld_out, P.elem, smem_cap)) c.push_back(kShapeSpmmGrouped);
+    if (spmm_grouped_fits(P.batch, op.ld_out, P.elem, smem_cap)) {
+      c.push_back(kShapeSpmmGrouped);
+      if (op.cols_p > 256) c.push_back(kShapeSpmmGrouped8);  // chunks of 256 columns
+    }
     c.push_back(kShapeSpmmDirect);
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
@@ -1132,13 +1285,16 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
     for (int v : {1, 2})
       if (ema_vertex_fits(P.batch, v, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap)) c.push_back(100 + v);
     if (P.elem == 4 && ema_reg_compiled(P.k - 1, op.a - 1, op.p, op.ema_sym)) c.push_back(kShapeEmaReg);
+    int upg = 1;
+    if (P.batch == 1 && ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg) > 0)
+      c.insert(c.begin(), kShapeEmaSched);
   }
   if (c.size() < 2) c.clear();
   return c;
 }
 
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
-                     bool build_tabs, Plan* out, const std::vector<int>* shapes, int colors, bool unpruned) {
+                     bool build_tabs, Plan* out, const std::vector<int>* shapes, int colors, int unpruned) {
   if (colors != 0 && (colors < t->k || colors > SGC_MAX_K))
     return fail(SGC_ERR_INVALID, "options.colors must be 0 or in [|T|, " + std::to_string(SGC_MAX_K) + "]");
   if (root >= t->k) return fail(SGC_ERR_INVALID, "options.root is not a template vertex");

@@ -175,9 +175,12 @@ struct PlanOp {
                              // batch with 8 / 12 entries per lane in flight, 10 private
                              // accumulator columns, 11 unrolled (8-bit positions, one 16-byte
                              // load per lane and neighbour), 12 wide (16-bit positions, one
-                             // 16-byte load per lane, neighbour and eight entries), 13 grouped
+                             // 16-byte load per lane, neighbour and eight entries), 14 one column
+                             // at a time (a thread per row and P column walks the row's neighbours:
+                             // the pruned sums without the row-wise SpMM), 13 grouped
                              // (a warp per row and coloring sums the rows of each neighbour color
-                             // in registers and scatters each color's sum once);
+                             // in registers and scatters each color's sum once; chunks of up to 512
+                             // columns), 15 the same with chunks of up to 256 columns;
                              // bucketed: 0 shared-memory buckets, 2 register buckets, 7 shared-
                              // memory buckets with a compile-time batch
   int spmm_pos_bytes = 0;    // direct: 0 = 32-bit position table read through L1; 1 or 2 =
@@ -185,6 +188,8 @@ struct PlanOp {
   int shape = 0;             // launch shape code (kSpmm* / eMA rows), see op_shape_candidates
   int ema_rows = 0;          // eMA: rows staged per block (32 * rows_per_lane, or 16..1)
   int ema_reg_k = 0;         // eMA: > 0 = the register form for K = ema_reg_k relative colors
+  int ema_sched = 0;         // eMA: > 0 = the scheduled form (one coloring per pass) staging this many rows
+  int ema_upg = 1;           // scheduled eMA: warps sharing one group of 32 outputs
   bool final_reg = false;    // last step: compile-time complement indices (k_final_reg)
   bool ema_final = false;    // eMA (register form, symmetric) fused with the last step that
                              // follows it: writes the last step's partials, not its table
@@ -243,13 +248,23 @@ constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
               kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14,
-              kShapeSpmmWide = 15, kShapeSpmmGrouped = 16;
+              kShapeSpmmWide = 15, kShapeSpmmGrouped = 16, kShapeSpmmGrouped8 = 17;
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
 // eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane) and the
 // register form (FP32, the (K, a-1, p, symmetric) shapes compiled in)
-constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103;
+constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103, kShapeEmaSched = 104;
+// the scheduled eMA (shape 104, one coloring per pass, kEmaSchedWarps warps per block): rows a block
+// stages (8, 4 or 2; 0 = does not fit) and shares of each group of 32 outputs' rounds
+constexpr int kEmaSchedWarps = 16;
+int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg);
+// words of one staged row: M_a row, P row (unless the table is combined with itself), 4 zero words
+inline int64_t ema_sched_rw(int64_t ld_a, int64_t ld_p, bool sym) { return ld_a + (sym ? 0 : ld_p) + 4; }
+inline int64_t ema_sched_smem(int rows, int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int upg) {
+  const int64_t G = (ct + 31) / 32;
+  return (int64_t)rows * ema_sched_rw(ld_a, ld_p, sym) * elem + (upg > 1 ? G * upg * 32 * rows * elem : 0) + 16;
+}
 // whether the register-form eMA is compiled in for K relative colors, an active
 // child of a vertices (a - 1 colors besides the root's) and a passive child of p
 bool ema_reg_compiled(int K, int a_minus_1, int p, bool sym);
@@ -286,10 +301,11 @@ inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4
 // are only built when build_tabs is set.  `shapes`, when given, holds one
 // launch-shape code per op index (0 = default); codes that do not fit the
 // op (shared memory, form) are ignored.  colors = number of colors (0: |T|).
-// unpruned: the ablation plan of Algorithm 1's loop order (OP_UNPRUNED ops).
+// unpruned: 1 = the ablation plan of Algorithm 1's loop order (OP_UNPRUNED ops); 2 = the
+// pruned plan with every SpMM taken one passive column at a time (thread per row and column).
 sgc_status make_plan(const sgc_graph* g, const sgc_template* t, int precision, int root, int policy, int batch,
                      bool build_tabs, Plan* out, const std::vector<int>* shapes = nullptr, int colors = 0,
-                     bool unpruned = false);
+                     int unpruned = 0);
 
 // The launch shapes worth timing for op `i` of plan p (empty: nothing to choose).
 std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& p, int i);

@@ -92,7 +92,7 @@ def test_recorded_sequence_replays_with_new_seeds(er_graph):
     assert launches[0] > 0 and launches[0] == launches[1] == launches[2]
 
 
-@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("spmm_shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_spmm_shape(precision, spmm_shape):
     sgc.build()
@@ -100,7 +100,7 @@ def test_every_spmm_shape(precision, spmm_shape):
     g = sgc.Graph(rp, ci)
     assert g.stats()["n_heavy"] > 0  # rows split into segments are covered
     # register buckets take one coloring per pass, the grouped form at most 4 (passes of 4, 4, 2, 1)
-    batch = 1 if spmm_shape == 4 else 4 if spmm_shape == 16 else 0
+    batch = 1 if spmm_shape == 4 else 4 if spmm_shape in (16, 17) else 0
     for parent in (sgcgen.pruefer_tree(8, 1008), sgcgen.spider_tree([3, 3, 3]), sgcgen.pruefer_tree(13, 7)):
         t = sgc.Template(parent)
         seeds = np.arange(1, 12 if len(parent) < 13 else 3, dtype=np.uint64)  # 8 + 2 + 1
@@ -122,6 +122,9 @@ def test_grouped_spmm(batch, precision):
         t = sgc.Template(parent)
         seeds = np.arange(90, 90 + 2 * batch + 1, dtype=np.uint64)  # passes of batch, batch, 1
         a = sgc.count(g, t, seeds, precision=precision, spmm_shape=16, batch=batch)
+        a8 = sgc.count(g, t, seeds, precision=precision, spmm_shape=17, batch=batch)
+        # the same terms; a position's color groups may come in another order across chunk borders
+        assert np.allclose(a.maps, a8.maps, rtol=1e-12 if precision == "fp64" else 1e-6, atol=0)
         if precision == "fp64":
             b = sgc.count(g, t, seeds, precision=precision, spmm_shape=8, batch=batch)
             assert np.array_equal(a.maps, b.maps) or np.allclose(a.maps, b.maps, rtol=1e-12, atol=0)
@@ -166,18 +169,21 @@ def test_unrolled_spmm_sums_in_the_same_order(batch):
         check(b.maps, oracle_maps(rp, ci, parent, seeds), "fp32")
 
 
-@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102, 103])
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102, 103, 104])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_ema_shape(ema_rows, precision):
     sgc.build()
     rp, ci = sgcgen.rmat(12, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=4)
     g = sgc.Graph(rp, ci)
     # the spider's eMA is symmetric (a table with itself), the others are not;
-    # vertex tiles need 4..32 colorings per pass: 16 + 8 + 1 exercises both kernels
-    for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8), sgcgen.spider_tree([3, 3, 3])):
+    # vertex tiles need 4..32 colorings per pass: 16 + 8 + 1 exercises both kernels;
+    # the scheduled form (104) takes one coloring per pass, tiles of 8 rows with a ragged last one
+    batch = 1 if ema_rows == 104 else 16
+    for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8), sgcgen.spider_tree([3, 3, 3]),
+                   sgcgen.pruefer_tree(13, 7)):
         t = sgc.Template(parent)
-        seeds = np.arange(20, 45, dtype=np.uint64)
-        r = sgc.count(g, t, seeds, precision=precision, ema_rows=ema_rows, batch=16)
+        seeds = np.arange(20, 45 if len(parent) < 13 else 22, dtype=np.uint64)
+        r = sgc.count(g, t, seeds, precision=precision, ema_rows=ema_rows, batch=batch)
         check(r.maps, oracle_maps(rp, ci, parent, seeds), precision)
 
 
@@ -266,3 +272,21 @@ def test_autotune_report_and_tuned_counts():
     seeds = np.arange(1, 12, dtype=np.uint64)
     tuned = sgc.count(g, t, seeds, precision="fp64", batch=8, autotune=True)
     check(tuned.maps, oracle_maps(rp, ci, parent, seeds), "fp64")
+
+
+def test_fused_combine_takes_no_table_workspace(monkeypatch):
+    # the 10-vertex spider's last combine runs fused with the last step: its 7-vertex table is never
+    # stored, so it takes no workspace and no HBM bytes (the same counts either way)
+    sgc.build()
+    rp, ci = sgcgen.rmat(12, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    parent = sgcgen.spider_tree([3, 3, 3])
+    fused = sgc.plan(sgc.Graph(rp, ci), sgc.Template(parent), batch=8)
+    seeds = np.arange(1, 9, dtype=np.uint64)
+    a = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, batch=8)
+    monkeypatch.setenv("SGC_NO_FUSE", "1")
+    g2 = sgc.Graph(rp, ci)
+    apart = sgc.plan(g2, sgc.Template(parent), batch=8)
+    b = sgc.count(g2, sgc.Template(parent), seeds, batch=8)
+    assert fused["workspace_bytes"] < apart["workspace_bytes"], (fused, apart)
+    assert fused["est_bytes"] < apart["est_bytes"]
+    assert np.allclose(a.maps, b.maps, rtol=1e-5, atol=0)
