@@ -199,10 +199,13 @@ def kernel_source_sha(function: str):
     return hashlib.sha256(src[m.start(1):end + 3].encode()).hexdigest()[:16]
 
 
-def recorded_traffic(op_name: str, k: int, batch: int):
+def recorded_traffic(op_name: str, k: int, batch: int, shape=None):
     """DRAM bytes per launch of an op from the committed ncu summary (profiles/traffic.json), if they were
     taken on the kernel's current source (the record keeps a hash of the kernel function's definition) for
-    the same op, number of colors and colorings per pass."""
+    the same op, number of colors, colorings per pass and launch shape (None: the shape is unknown, and no
+    record applies)."""
+    if shape is None:
+        return None
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -210,7 +213,8 @@ def recorded_traffic(op_name: str, k: int, batch: int):
     except Exception:
         return None
     for r in rec.get("kernels", []):
-        if r.get("op") == op_name and r.get("k") == k and r.get("batch") == batch and r.get("function") and \
+        if r.get("op") == op_name and r.get("k") == k and r.get("batch") == batch and r.get("shape") == shape and \
+                r.get("function") and \
                 r.get("function_sha") == kernel_source_sha(r["function"]):
             return r.get("dram_bytes_per_launch")
     return None
@@ -833,10 +837,15 @@ def main():
     res["clocks"] = clocks
     # the remaining measurements run after the timed region, on steps of their own
     extra = W + K
+    chosen = {}  # (k, op, colorings per pass) -> the launch shape the autotuner kept
     if tune:
         res["tuned_shapes"] = {}
-        for name, t in templates:
+        for (name, t), (_, spec) in zip(templates, wl["templates"]):
             rep = sgc.sgc_autotune(g.handle, t.handle, opt32)
+            for e in rep:
+                if e["kind"] >= 0:
+                    chosen[(len(make_parent(spec)), f"{e['name']}(t={e['t']},a={e['a']},p={e['p']})", e["batch"])] = \
+                        e["shapes"][e["chosen"]]
             res["tuned_shapes"][name] = [
                 (f"{e['name']}(t={e['t']},a={e['a']},p={e['p']},B={e['batch']})" if e["kind"] >= 0 else "batch") +
                 ": " + ", ".join(f"{sgc.SHAPE_NAMES.get(sh, sh) if e['kind'] == 2 else sh}={m:.2f}ms"
@@ -882,7 +891,9 @@ def main():
     ops.sort(key=lambda o: -o["share"])
     dom = ops[0]
     res["roofline"] = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
-                       "traffic": recorded_traffic(dom["op"], dom["k"], dom["batch"]), "kernel": dom["op"],
+                       "traffic": recorded_traffic(dom["op"], dom["k"], dom["batch"],
+                                                   chosen.get((dom["k"], dom["op"], dom["batch"]))),
+                       "kernel": dom["op"], "launch_shape": chosen.get((dom["k"], dom["op"], dom["batch"])),
                        "k": dom["k"], "colorings_per_launch": dom["batch"],
                        "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else '6.8 TB/s'}, burst copy)",
                        "bytes_per_launch": dom["survey_bytes_per_pass"],

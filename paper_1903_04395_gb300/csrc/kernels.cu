@@ -1347,7 +1347,8 @@ __global__ void __launch_bounds__(kBlock) k_spmm_g(
       };
       int cur = -1;
       // neighbour t's row entries are loaded while neighbour t - 1's are added (and a finished
-      // group's sum is added into the output row), so two neighbours' loads are in flight
+      // group's sum is added into the output row), so two neighbours' loads are in flight (four,
+      // measured, cost more registers than they hide latency)
       auto load = [&](int32_t u, T (&x)[NR]) {
         const T* src = Min + ((int64_t)u * ld_in + jl) * B + b;
 #pragma unroll

@@ -31,13 +31,15 @@ def test_recorded_traffic_follows_the_function_hash(monkeypatch):
     r = rec["kernels"][0]
     # with the recorded hash the record is used; with any other hash it reads as unmeasured
     monkeypatch.setattr(b, "kernel_source_sha", lambda fn: r["function_sha"])
-    assert b.recorded_traffic(r["op"], r["k"], r["batch"]) == r["dram_bytes_per_launch"]
-    # another number of colors or colorings per pass is another launch
-    assert b.recorded_traffic(r["op"], r["k"] + 1, r["batch"]) is None
-    assert b.recorded_traffic(r["op"], r["k"], r["batch"] * 2) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"], r["shape"]) == r["dram_bytes_per_launch"]
+    # another number of colors, colorings per pass or launch shape is another launch
+    assert b.recorded_traffic(r["op"], r["k"] + 1, r["batch"], r["shape"]) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"] * 2, r["shape"]) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"], r["shape"] + 1) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"], None) is None
     monkeypatch.setattr(b, "kernel_source_sha", lambda fn: "0" * 16)
-    assert b.recorded_traffic(r["op"], r["k"], r["batch"]) is None
-    assert b.recorded_traffic("no such op", r["k"], r["batch"]) is None
+    assert b.recorded_traffic(r["op"], r["k"], r["batch"], r["shape"]) is None
+    assert b.recorded_traffic("no such op", r["k"], r["batch"], r["shape"]) is None
 
 
 def test_survey_bytes_formulas():
