@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="colorings per pass override")
     ap.add_argument("--spmm-shape", type=int, default=0, help="force an SpMM launch shape (sgc_options.spmm_shape)")
     ap.add_argument("--ema-rows", type=int, default=0, help="force an eMA launch shape (sgc_options.ema_rows)")
+    ap.add_argument("--root", type=int, default=-1,
+                    help="force the DP root (sgc_options.root; profiling a small graph with a large one's plan)")
     ap.add_argument("--template", action="append", default=None,
                     help="only these templates of the workload (profiling small cases; not a bench configuration)")
     ap.add_argument("--rcm", action="store_true",
@@ -820,7 +822,7 @@ def main():
         return ms, g.stats()["kernel_launches"] - l0, (sampler.summary() if sampler else None)
 
     tune = 0 if (args.no_autotune or args.spmm_shape or args.ema_rows) else 1
-    opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream,
+    opt32 = sgc.sgc_options_init(precision=sgc.SGC_FP32, batch=B, stream=stream.cuda_stream, root=args.root,
                                  spmm_shape=args.spmm_shape, ema_rows=args.ema_rows, autotune=tune)
     t_w = time.perf_counter()
     run_steps(opt32, 0, W)  # warm-up: plans, autotuning (first call per template), CUDA-graph recording

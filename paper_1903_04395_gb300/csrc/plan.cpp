@@ -602,8 +602,11 @@ int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, i
   }
   *upg = G < W ? (int)(W / gcd) : 1;
   if (ema_sched_rw(ld_a, ld_p, sym) >= 65535) return 0;  // every word of a row has a 16-bit index
-  for (int r : {8, 4, 2})
-    if (ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= smem_cap) return r;
+  // at most 200 KB of the block's shared memory: under ncu a launch of this kernel that asked for
+  // 218 of the 227 KB failed (the plain run of the same program did not)
+  const int64_t cap = std::min<int64_t>(smem_cap, 200 * 1024);
+  for (int r : {8, 6, 4, 2})
+    if (ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= cap) return r;
   return 0;
 }
 

@@ -256,7 +256,7 @@ constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
 // register form (FP32, the (K, a-1, p, symmetric) shapes compiled in)
 constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103, kShapeEmaSched = 104;
 // the scheduled eMA (shape 104, one coloring per pass, kEmaSchedWarps warps per block): rows a block
-// stages (8, 4 or 2; 0 = does not fit) and shares of each group of 32 outputs' rounds
+// stages (8, 6, 4 or 2 within 200 KB; 0 = does not fit) and shares of each group of 32 outputs' rounds
 constexpr int kEmaSchedWarps = 16;
 int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg);
 // words of one staged row: M_a row, P row (unless the table is combined with itself), 4 zero words
