@@ -149,6 +149,14 @@ sgc_options resolve(const sgc_options* opt) {
 // Plans for every power-of-two batch up to bmax that fits mem_limit; the
 // root and cut order come from the cost model once and are shared.  Cached on
 // the graph per (template, precision, root, bmax).
+// the largest workspace among a plan set's batch sizes (a pass of one coloring can need more than a
+// larger batch's: the grouped SpMM's neighbour-group buffers)
+static int64_t max_ws(const PlanSet& set) {
+  int64_t ws = 0;
+  for (const auto& kv : set.by_batch) ws = std::max(ws, kv.second.ws_bytes);
+  return ws;
+}
+
 sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_options& o, int bmax, int64_t mem_limit,
                         std::shared_ptr<PlanSet>* out) {
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
@@ -156,7 +164,7 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
                           std::to_string(o.spmm_shape) + "/e" + std::to_string(o.ema_rows) + "/c" +
                           std::to_string(o.colors) + (o.unpruned ? "/unpruned" + std::to_string(o.unpruned) : "");
   for (auto& kv : g->plan_cache)
-    if (kv.first == key && kv.second->by_batch.at(kv.second->bfit).ws_bytes <= mem_limit) {
+    if (kv.first == key && max_ws(*kv.second) <= mem_limit) {
       *out = kv.second;
       return SGC_OK;
     }

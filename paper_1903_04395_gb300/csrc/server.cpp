@@ -122,11 +122,16 @@ void give_range(sgc_server* s, int64_t off, int64_t len) {
   s->free_ranges.swap(merged);
 }
 
-// bytes a request needs: its top plan's workspace plus device room for seeds and results
-int64_t request_bytes(const Request& r) {
-  const Plan& top = r.plans->by_batch.at(r.plans->bfit);
-  return (top.ws_bytes + 255) / 256 * 256 + (int64_t)r.seeds.size() * 16 + 256;
+// workspace a request's passes need: the largest of its plans' (a pass of fewer colorings can need
+// more than the top plan: one coloring per pass adds the neighbour-group buffers of the grouped SpMM)
+int64_t request_ws(const Request& r) {
+  int64_t ws = 0;
+  for (const auto& kv : r.plans->by_batch) ws = std::max(ws, kv.second.ws_bytes);
+  return (ws + 255) / 256 * 256;
 }
+
+// bytes a request needs: its workspace plus device room for seeds and results
+int64_t request_bytes(const Request& r) { return request_ws(r) + (int64_t)r.seeds.size() * 16 + 256; }
 
 void finish(sgc_server* s, const std::shared_ptr<Request>& r, sgc_status st, const std::string& err) {
   r->status = st;
@@ -165,9 +170,9 @@ sgc_status launch(sgc_server* s, const std::shared_ptr<Request>& r, int slot) {
   r->st = s->streams[(size_t)priority_level(s, *r)][(size_t)slot];
   cudaStream_t st = r->st;
   char* base = s->arena + r->off;
-  const Plan& top = r->plans->by_batch.at(r->plans->bfit);
   char* ws = base;
-  uint64_t* d_seeds = reinterpret_cast<uint64_t*>(base + (top.ws_bytes + 255) / 256 * 256);
+  const int64_t ws_len = request_ws(*r);
+  uint64_t* d_seeds = reinterpret_cast<uint64_t*>(base + ws_len);
   double* d_maps = reinterpret_cast<double*>(d_seeds + r->seeds.size());
   const int32_t n = (int32_t)r->seeds.size();
   SGC_CUDA_TRY(cudaMemcpyAsync(d_seeds, r->seeds.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
@@ -175,6 +180,7 @@ sgc_status launch(sgc_server* s, const std::shared_ptr<Request>& r, int slot) {
     int b = r->plans->bfit;
     while (b > n - i) b /= 2;
     const Plan& plan = r->plans->by_batch.at(b);
+    if (plan.ws_bytes > ws_len) return fail(SGC_ERR_INTERNAL, "a pass's workspace exceeds the request's range");
     SGC_CUDA_TRY(cudaMemcpyAsync(ws + plan.bufs[plan.buf_seeds].offset, d_seeds + i, sizeof(uint64_t) * b,
                                  cudaMemcpyDeviceToDevice, st));
     int64_t nk = 0;
@@ -221,9 +227,8 @@ void scheduler(sgc_server* s) {
       const cudaError_t q = cudaEventQuery(s->events[slot]);
       if (q == cudaErrorNotReady) continue;
       if (q == cudaSuccess) {
-        const Plan& top = r->plans->by_batch.at(r->plans->bfit);
-        const double* d_maps = reinterpret_cast<const double*>(
-            s->arena + r->off + (top.ws_bytes + 255) / 256 * 256 + (int64_t)r->seeds.size() * 8);
+        const double* d_maps = reinterpret_cast<const double*>(s->arena + r->off + request_ws(*r) +
+                                                               (int64_t)r->seeds.size() * 8);
         r->maps.assign(r->seeds.size(), 0.0);
         cudaError_t e = cudaMemcpyAsync(r->maps.data(), d_maps, sizeof(double) * r->maps.size(),
                                         cudaMemcpyDeviceToHost, r->st);

@@ -114,3 +114,29 @@ def test_destroy_with_queued_requests(graph):
     for i in range(20):
         srv.submit(t, list(range(i * 8, i * 8 + 8)))
     srv.close()  # cancels what has not started, waits for what runs; must not hang
+
+
+def test_passes_of_fewer_colorings_fit_the_request_range():
+    # a request's last passes take fewer colorings; a pass of one coloring uses the grouped SpMM and
+    # its neighbour-group buffers, which on a graph with many stored entries make its workspace larger
+    # than the top pass's: every pass must still fit the range the server gave the request, and the
+    # results equal sgc_count's, alone and side by side
+    sgc.build()
+    rp, ci = sgcgen.rmat(16, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1)
+    g = sgc.Graph(rp, ci)
+    parent = sgcgen.path_tree(4)
+    t = sgc.Template(parent)
+    assert sgc.plan(g, t, batch=1)["workspace_bytes"] > sgc.plan(g, t, batch=2)["workspace_bytes"]
+    queries = [(parent, [1, 2, 3], "fp64"), (parent, [4, 5, 6, 7, 8], "fp64"),
+               (sgcgen.pruefer_tree(6, 3), [9, 10, 11], "fp32")]
+    want = [sgc.count(g, sgc.Template(p), s, precision=prec).maps for p, s, prec in queries]
+    for mixed in (False, True):
+        out, stats = _run(g, queries * (2 if mixed else 1), mixed=mixed, budget=8 << 30)
+        assert stats["failed"] == 0
+        for i, (_, seeds, prec) in enumerate(queries * (2 if mixed else 1)):
+            got = out[i][1]
+            ref = want[i % len(queries)]
+            if prec == "fp64":
+                assert np.array_equal(got, ref), (i, got, ref)
+            else:
+                assert np.allclose(got, ref, rtol=FP32_RTOL, atol=0), (i, got, ref)
