@@ -1590,11 +1590,16 @@ __global__ void __launch_bounds__(32 * kEmaSchedWarps) k_ema_s(
       T acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[r] = T(0);
-      // eight rounds' table words are loaded before they are used (the table streams from L2)
-      for (uint32_t j = j0; j < j1; j += 8) {
-        uint32_t ev[8];
+      // table words come eight rounds at a time, the next eight loaded while these are used (the
+      // table streams from L2)
+      uint32_t ev[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ev[q] = j + q < j1 ? __ldg(tp + (int64_t)(j + q) * 32) : 0xFFFFFFFFu;
+      for (int q = 0; q < 8; ++q) ev[q] = j0 + q < j1 ? __ldg(tp + (int64_t)(j0 + q) * 32) : 0xFFFFFFFFu;
+      for (uint32_t j = j0; j < j1; j += 8) {
+        uint32_t en[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          en[q] = j + 8 + q < j1 ? __ldg(tp + (int64_t)(j + 8 + q) * 32) : 0xFFFFFFFFu;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const uint32_t e = ev[q] == 0xFFFFFFFFu ? idle_e : ev[q];  // idle: the zero word (no branch)
@@ -1603,6 +1608,8 @@ __global__ void __launch_bounds__(32 * kEmaSchedWarps) k_ema_s(
 #pragma unroll
           for (int r = 0; r < R; ++r) acc[r] += pa[(int64_t)r * rw] * pp[(int64_t)r * rw];
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ev[q] = en[q];
       }
       const int S = g * 32 + lane;
       if (upg == 1) {
