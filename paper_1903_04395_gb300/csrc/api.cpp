@@ -157,6 +157,18 @@ static int64_t max_ws(const PlanSet& set) {
   return ws;
 }
 
+// Untuned plan sets depend on the graph only through its sizes (active vertices, stored entries,
+// heavy rows and their segments) and the device's SM count and shared memory, so they are also kept
+// process-wide: a new handle for a graph of the same shape (a graph uploaded again) reuses them.
+// Tuned sets hold measurements of one graph and stay with it.
+static std::mutex g_shared_plans_mu;
+static std::vector<std::pair<std::string, std::shared_ptr<PlanSet>>> g_shared_plans;
+
+static std::string graph_signature(const sgc_graph* g) {
+  return std::to_string(g->n_act) + "," + std::to_string(g->nnz) + "," + std::to_string(g->n_heavy) + "," +
+         std::to_string(g->n_seg) + "," + std::to_string(g->num_sms) + "," + std::to_string(g->smem_optin) + "|";
+}
+
 sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_options& o, int bmax, int64_t mem_limit,
                         std::shared_ptr<PlanSet>* out) {
   const std::string key = std::to_string(t->uid) + "/" + std::to_string(o.precision) + "/" + std::to_string(o.root) +
@@ -168,6 +180,17 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
       *out = kv.second;
       return SGC_OK;
     }
+  const std::string shared_key = graph_signature(g) + key;
+  if (!o.autotune) {
+    std::lock_guard<std::mutex> lock(g_shared_plans_mu);
+    for (auto& kv : g_shared_plans)
+      if (kv.first == shared_key && max_ws(*kv.second) <= mem_limit) {
+        if (g->plan_cache.size() >= 64) g->plan_cache.erase(g->plan_cache.begin());
+        g->plan_cache.push_back({key, kv.second});
+        *out = kv.second;
+        return SGC_OK;
+      }
+  }
   auto set = std::make_shared<PlanSet>();
   const bool forced = o.spmm_shape != 0 || o.ema_rows != 0;
   // forced launch shapes, as one code per op index of a plan
@@ -220,6 +243,11 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     }
   if (g->plan_cache.size() >= 64) g->plan_cache.erase(g->plan_cache.begin());
   g->plan_cache.push_back({key, set});
+  if (!o.autotune) {
+    std::lock_guard<std::mutex> lock(g_shared_plans_mu);
+    if (g_shared_plans.size() >= 64) g_shared_plans.erase(g_shared_plans.begin());
+    g_shared_plans.push_back({shared_key, set});
+  }
   *out = set;
   return SGC_OK;
 }
