@@ -1934,10 +1934,18 @@ __global__ void __launch_bounds__(128, SYM ? 3 : 2) k_ema_reg(const float* __res
 }
 
 // the (K, a-1, p, symmetric) shapes compiled in: the 10-color spider's combine
-// of a 3-vertex leg with the root and another leg (and its symmetric form)
+// of a 3-vertex leg with the root and another leg (and its symmetric form), and
+// the combines the 7-, 8- and 11-vertex Pruefer trees (seeds 1007, 1008, 1011)
+// plan at 8 or more colorings per pass, whose passive and output rows fit in
+// registers (C(K, p) + C(K, a-1+p) at most 165 floats)
 #define SGC_EMA_REG_SHAPES(X) \
   X(9, 3, 3, false)           \
-  X(9, 3, 3, true)
+  X(9, 3, 3, true)            \
+  X(6, 3, 2, false)           \
+  X(7, 1, 1, true)            \
+  X(10, 2, 1, false)          \
+  X(10, 1, 1, true)           \
+  X(10, 5, 3, false)
 
 // ----------------------------------------------- last step + vertex sum --
 // maps_b = sum_v sum_{C_p} M_a(v, [k] \ C_p) * P(v, C_p).  One thread per row

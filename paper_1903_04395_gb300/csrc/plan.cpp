@@ -1036,9 +1036,11 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
         op.ema_vrpl = shape - 100;
       }
       op.ema_sym = op.in_a == op.in_p && A.size - 1 == Pc.size;
-      // the register form (FP32, compiled-in shapes): the default where it exists
+      // the register form (FP32, compiled-in shapes): forced, or the default where it exists at 8 or
+      // more colorings per pass (a thread holds one (vertex, coloring) row: its loads coalesce only
+      // across interleaved colorings)
       if (elem == 4 && ema_reg_compiled(K, A.size - 1, Pc.size, op.ema_sym) &&
-          (shape == 0 || shape == kShapeEmaReg)) {
+          ((shape == 0 && batch >= 8) || shape == kShapeEmaReg)) {
         op.ema_reg_k = K;
         op.ema_vrpl = 0;
       }

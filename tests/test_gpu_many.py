@@ -290,3 +290,20 @@ def test_fused_combine_takes_no_table_workspace(monkeypatch):
     assert fused["workspace_bytes"] < apart["workspace_bytes"], (fused, apart)
     assert fused["est_bytes"] < apart["est_bytes"]
     assert np.allclose(a.maps, b.maps, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("batch", [8, 16, 32])
+def test_register_ema_shapes_of_the_batched_trees(batch):
+    # the register-form combines compiled in for the 7-, 8- and 11-vertex Pruefer trees (seeds 1007,
+    # 1008, 1011): the vertex tiles' sums (FP32 rounding apart) and the oracle's counts
+    sgc.build()
+    rp, ci = sgcgen.rmat(12, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=5)
+    g = sgc.Graph(rp, ci)
+    for k in (7, 8, 11):
+        parent = sgcgen.pruefer_tree(k, 1000 + k)
+        t = sgc.Template(parent)
+        seeds = np.arange(200, 200 + batch, dtype=np.uint64)
+        a = sgc.count(g, t, seeds, precision="fp32", batch=batch, ema_rows=103)
+        b = sgc.count(g, t, seeds, precision="fp32", batch=batch, ema_rows=101)
+        assert np.allclose(a.maps, b.maps, rtol=1e-6, atol=0), (k, a.maps, b.maps)
+        check(a.maps[:4], oracle_maps(rp, ci, parent, seeds[:4]), "fp32")
