@@ -94,16 +94,22 @@ typedef struct sgc_options {
                           batch, 16 grouped (1, 2 or 4 colorings per pass: a warp per row and
                           coloring sums the rows of each neighbour color in registers and adds each
                           color's sum into the output row once; columns in chunks of up to 512),
-                          17 grouped in chunks of up to 256 columns; ops it does not fit keep
-                          theirs.  0 (default) = planner or
+                          17 grouped in chunks of up to 256 columns, 18 grouped with the
+                          neighbour rows copied into a ring of 4 shared-memory chunks of up to
+                          1,024 columns per warp (FP32, one coloring per pass, rows wider than 128
+                          columns), 19 the same with a ring of 8 chunks of up to 512 columns; ops
+                          it does not fit keep theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per
                           block, or 101 / 102 = whole vertex rows copied asynchronously in tiles,
                           1 / 2 rows per lane (4..32 colorings per pass), or 103 = every operand in
-                          registers (FP32; the shapes compiled in: 10 colors with a 3-color passive
-                          child and a 3-color active one, the default where it applies), or 104 =
-                          scheduled (one coloring per pass: 8 rows staged by bulk copies, each
-                          output's split terms in rounds that read distinct shared-memory banks);
+                          registers (FP32; the shapes compiled in: 10 colors with 3-color active and
+                          passive children, and the 7-, 8- and 11-color trees' combines with narrow
+                          rows; the default where it applies at 8 or more colorings per pass), or
+                          104 = scheduled (one coloring per pass: up to 8 rows staged by bulk copies
+                          in at most 200 KB, each output's split terms in rounds that read distinct
+                          shared-memory banks), or 105 = scheduled with half as many rows, so that
+                          two blocks share an SM (one stages its rows while the other computes);
                           ops it does not fit keep theirs; 0 (default) = planner or autotuner */
   int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
                           |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have

@@ -531,12 +531,13 @@ sgc_status count_core(const sgc_graph* g, int32_t n_t, const sgc_template* const
   }
   if (o.batch < 0) return fail(SGC_ERR_INVALID, "options.batch must be >= 0");
   if (o.unpruned < 0 || o.unpruned > 2) return fail(SGC_ERR_INVALID, "options.unpruned must be 0, 1 or 2");
-  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmGrouped8)
-    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0.." + std::to_string(kShapeSpmmGrouped8));
+  if (o.spmm_shape < 0 || o.spmm_shape > kShapeSpmmStaged8)
+    return fail(SGC_ERR_INVALID, "options.spmm_shape must be 0.." + std::to_string(kShapeSpmmStaged8));
   if (o.ema_rows != 0 && o.ema_rows != 64 && o.ema_rows != 32 && o.ema_rows != 16 && o.ema_rows != 8 &&
       o.ema_rows != 4 && o.ema_rows != 2 && o.ema_rows != 1 && o.ema_rows != kShapeEmaVertex1 &&
-      o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg && o.ema_rows != kShapeEmaSched)
-    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101, 102, 103 or 104");
+      o.ema_rows != kShapeEmaVertex2 && o.ema_rows != kShapeEmaReg && o.ema_rows != kShapeEmaSched &&
+      o.ema_rows != kShapeEmaSched2)
+    return fail(SGC_ERR_INVALID, "options.ema_rows must be 0, 64, 32, 16, 8, 4, 2, 1, 101, 102, 103, 104 or 105");
   SGC_CUDA_TRY(cudaSetDevice(g->device));
   std::lock_guard<std::mutex> lock(g->mu);
   DevicePool& pool = device_pool(g->device);

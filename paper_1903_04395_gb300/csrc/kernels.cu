@@ -1392,6 +1392,177 @@ __global__ void __launch_bounds__(kBlock) k_spmm_g(
   }
 }
 
+// Staged grouped form (one coloring per pass, FP32): the sums of k_spmm_g, with
+// the neighbour rows and the output positions copied into shared memory by
+// 16-byte asynchronous copies (cp.async) instead of loaded into registers.  A
+// warp's work is one sequence of entries: its items w0, w0 + S, ... (S warps in
+// the grid), within an item the chunks of CH = 128 NR4 columns, within a chunk
+// the kept neighbours in group order.  The copies run RS entries of it ahead
+// of the entry being summed, across chunk and item boundaries: entry e's chunk
+// of its neighbour's row goes to slot e % RS of a ring, and the first entry of
+// a color group also copies the group's chunk of the position table (row pitch
+// wp, a multiple of 8) into a ring of RS + 1 position buffers - the copies are
+// at most RS groups ahead, so they never overwrite the group being summed.
+// Every step commits one copy group (an empty one once the sequence is used
+// up): the entry at the head has landed when all but the newest RS - 1 groups
+// are done.  Lane l sums the columns j0 + 128 r + 4 l + q (r < NR4, q < 4).
+// Per position the sums run in k_spmm_g's order (CSR order within a color,
+// colors ascending): the same results.
+template <int NR4, int RS>
+__global__ void __launch_bounds__(512) k_spmm_gs(
+    const int32_t* __restrict__ row_ptr, int32_t n_seg, const int32_t* __restrict__ seg_row,
+    const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_hi, int32_t n_heavy, int32_t n_act,
+    const uint8_t* __restrict__ colors, int k, const int32_t* __restrict__ gids, const uint8_t* __restrict__ gcols,
+    const int32_t* __restrict__ gkept, const float* __restrict__ Min, int w_in, int ld_in, float* __restrict__ P,
+    int ld_out, float* __restrict__ scratch, const uint16_t* __restrict__ tab, int wp, const ScaleState* st_in,
+    ScaleState* st_out) {
+  constexpr int CH = 128 * NR4;  // columns per chunk
+  constexpr int PB = RS + 1;     // position buffers
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  // a warp's words: its output row, RS row chunks, PB chunks of 16-bit positions, RS group colors
+  const int64_t per_warp = (int64_t)ld_out + RS * CH + PB * CH / 2 + (RS + 3) / 4 * 4;
+  float* acc = reinterpret_cast<float*>(sm_raw) + warp * per_warp;
+  float* slots = acc + ld_out;
+  uint16_t* pbufs = reinterpret_cast<uint16_t*>(slots + RS * CH);
+  int* slot_c = reinterpret_cast<int*>(slots + RS * CH + PB * CH / 2);
+  const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
+  const int64_t S = (int64_t)gridDim.x * wpb;
+  const int nch = (w_in + CH - 1) / CH;
+
+  // the copies' cursor: item lw (lkept kept entries from llo on, row color lcv), chunk lc, entry
+  // le; the ids and colors of the entries' block of 32 in lane registers; the last group's color
+  int64_t lw = (int64_t)blockIdx.x * wpb + warp;
+  int lc = 0, le = 0, lkept = 0, llo = 0, lcv = 0, lblk = -1, lprev = -1, lpb = 0;
+  int32_t lid = 0;
+  int lcol = 0;
+  auto seek = [&](int64_t w) -> int64_t {  // the first item from w on with kept entries
+    for (; w < nitems; w += S) {
+      const int kk = gkept[w];
+      if (kk > 0) {
+        const SpmmItem it = spmm_item(w, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+        lkept = kk;
+        llo = it.lo;
+        lcv = colors[it.row];
+        lblk = -1;
+        break;
+      }
+    }
+    return w;
+  };
+  auto issue = [&](int slot) {
+    if (lw < nitems) {
+      const int blk = le >> 5;
+      if (blk != lblk) {
+        const int e = (blk << 5) + lane;
+        lid = e < lkept ? __ldg(gids + llo + e) : 0;
+        lcol = e < lkept ? (int)__ldg(gcols + llo + e) : 0;
+        lblk = blk;
+      }
+      const int32_t u = __shfl_sync(full, lid, le & 31);
+      const int c = __shfl_sync(full, lcol, le & 31);
+      const int j0 = lc * CH;
+      const int nv = (min(CH, w_in - j0) + 3) >> 2;  // 16-byte pieces of the row chunk
+      const float* src = Min + (int64_t)u * ld_in + j0;
+      float* dst = slots + slot * CH;
+#pragma unroll
+      for (int r = 0; r < NR4; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nv) cp_async16(dst + 4 * i, src + 4 * i);
+      }
+      if (c != lprev) {  // a group starts: its chunk of positions
+        const int np = min(CH, wp - j0) >> 3;  // 16-byte pieces of 8 positions
+        const uint16_t* ps = tab + ((int64_t)lcv * k + c) * wp + j0;
+        uint16_t* pd = pbufs + lpb * CH;
+        for (int i = lane; i < np; i += 32) cp_async16(pd + 8 * i, ps + 8 * i);
+        lpb = lpb + 1 == PB ? 0 : lpb + 1;
+        lprev = c;
+      }
+      if (lane == 0) slot_c[slot] = c;
+      if (++le == lkept) {
+        le = 0;
+        lprev = -1;
+        if (++lc == nch) {
+          lc = 0;
+          lw = seek(lw + S);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  lw = seek(lw);
+  for (int i = 0; i < RS; ++i) issue(i);
+  float m = 0.f;
+  int slot = 0, cpb = 0;
+  for (int64_t w = (int64_t)blockIdx.x * wpb + warp; w < nitems; w += S) {
+    const SpmmItem it = spmm_item(w, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+    const int kept = gkept[w];
+    float4* acc4 = reinterpret_cast<float4*>(acc);
+    for (int i = lane; i < ld_out / 4; i += 32) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    for (int ch = 0; kept > 0 && ch < nch; ++ch) {
+      const int j0 = ch * CH;
+      float a[NR4][4];
+#pragma unroll
+      for (int r = 0; r < NR4; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+      int cur = -1;
+      const uint16_t* pos = pbufs;
+      auto flush = [&]() {
+#pragma unroll
+        for (int r = 0; r < NR4; ++r) {
+          const int jb = j0 + 128 * r + 4 * lane;
+          const uint2 pw = *reinterpret_cast<const uint2*>(pos + 128 * r + 4 * lane);
+          const uint32_t p4[4] = {pw.x & 0xffffu, pw.x >> 16, pw.y & 0xffffu, pw.y >> 16};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (jb + q < w_in && p4[q] != 0xFFFFu) acc[p4[q]] += a[r][q];
+            a[r][q] = 0.f;
+          }
+        }
+        __syncwarp();
+      };
+      for (int e = 0; e < kept; ++e) {
+        cp_async_wait<RS - 1>();
+        __syncwarp();
+        const int c = slot_c[slot];
+        if (c != cur) {
+          if (cur >= 0) flush();
+          cur = c;
+          pos = pbufs + cpb * CH;
+          cpb = cpb + 1 == PB ? 0 : cpb + 1;
+        }
+        const float4* s4 = reinterpret_cast<const float4*>(slots + slot * CH) + lane;
+#pragma unroll
+        for (int r = 0; r < NR4; ++r) {
+          const float4 x = s4[32 * r];
+          a[r][0] += x.x;
+          a[r][1] += x.y;
+          a[r][2] += x.z;
+          a[r][3] += x.w;
+        }
+        __syncwarp();
+        issue(slot);
+        slot = slot + 1 == RS ? 0 : slot + 1;
+      }
+      if (cur >= 0) flush();
+    }
+    float* dst = it.heavy ? scratch + w * (int64_t)ld_out : P + (int64_t)it.row * ld_out;
+    float4* dst4 = reinterpret_cast<float4*>(dst);
+    for (int i = lane; i < ld_out / 4; i += 32) {
+      const float4 v = acc4[i];
+      dst4[i] = v;
+      if (!it.heavy) m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  publish_max(st_out, m);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st_out->e = st_in->e;
+}
+
 // ------------------------------------------------------- general eMA --
 // M_s(v, S) = sum over the splits (A, S \ A) of M_a(v, A) * P(v, S \ A).
 // A block stages R consecutive rows of M_a and P in shared memory as
@@ -2647,6 +2818,44 @@ sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanO
     ++*nk;
     *ready = true;
   }
+  if (op.spmm_variant == 16 || op.spmm_variant == 17) {
+    // the staged form: one block per SM of as many warps (at most 16) as shared memory holds
+    if constexpr (std::is_same<T, float>::value) {
+      if (batch != 1) return fail(SGC_ERR_INTERNAL, "staged SpMM: one coloring per pass");
+      const int nr4 = spmm_staged_nr4(op.cols_p, op.spmm_variant), rs = spmm_staged_rs(op.spmm_variant);
+      const size_t pw = (size_t)spmm_staged_warp_bytes(op.cols_p, op.ld_out, op.spmm_variant);
+      const int wn = (int)std::min<size_t>(16, smem_cap / pw);
+      if (wn < 2) return fail(SGC_ERR_UNSUPPORTED, "staged SpMM: two warps' rings do not fit in shared memory");
+      if (reinterpret_cast<uintptr_t>(M) % 16 || reinterpret_cast<uintptr_t>(tab) % 16 ||
+          reinterpret_cast<uintptr_t>(P) % 16 || reinterpret_cast<uintptr_t>(scratch) % 16 || op.ld_p % 4 ||
+          op.ld_out % 4)
+        return fail(SGC_ERR_INTERNAL, "staged SpMM: rows and tables must start on 16-byte boundaries");
+      const size_t smem = pw * wn;
+      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms, (nitems + wn - 1) / wn));
+      const uint16_t* tab16 = reinterpret_cast<const uint16_t*>(tab);
+      const int wpitch = (int)spmm_staged_pitch(op.cols_p);
+#define SGC_GS(NR4_, RS_)                                                                                    \
+  do {                                                                                                       \
+    allow_smem(k_spmm_gs<NR4_, RS_>, smem);                                                                  \
+    k_spmm_gs<NR4_, RS_><<<grid, 32 * wn, smem, st>>>(g->d_row_ptr, g->n_seg, g->d_seg_row, g->d_seg_lo,    \
+                                                      g->d_seg_hi, g->n_heavy, g->n_act, colors, plan.k, gids, \
+                                                      gcols, gkept, M, (int)op.cols_p, (int)op.ld_p, P,      \
+                                                      (int)op.ld_out, scratch, tab16, wpitch, si, so);       \
+  } while (0)
+      if (rs == 8) {
+        if (nr4 == 2) SGC_GS(2, 8);
+        else SGC_GS(4, 8);
+      } else {
+        if (nr4 == 2) SGC_GS(2, 4);
+        else if (nr4 == 4) SGC_GS(4, 4);
+        else SGC_GS(8, 4);
+      }
+#undef SGC_GS
+      ++*nk;
+    } else {
+      return fail(SGC_ERR_INTERNAL, "staged SpMM: FP32 tables only");
+    }
+  } else {
   const size_t per_warp = (size_t)op.ld_out * sizeof(T);
   int w = wpb;
   while (w > 2 && per_warp * w > smem_cap) w /= 2;
@@ -2681,6 +2890,7 @@ sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanO
 #undef SGC_G2
 #undef SGC_G
   ++*nk;
+  }
   if (g->n_heavy > 0) {
     constexpr int VN = Vec16<T>::n;
     const int64_t width = (int64_t)batch * op.ld_out;
@@ -2782,7 +2992,7 @@ sgc_status run_pass_t(const sgc_graph* g, const Plan& plan, const uint32_t* d_ta
           ++nk;
           break;
         }
-        if (op.spmm_variant == 13 || op.spmm_variant == 15) {
+        if (spmm_variant_grouped(op.spmm_variant)) {
           sgc_status rc = launch_spmm_grouped<T>(g, plan, op, B, colors, reinterpret_cast<const T*>(buf(op.in_p)),
                                                  reinterpret_cast<T*>(buf(op.out)), scratch, d_tabs + op.tab_off,
                                                  reinterpret_cast<int32_t*>(buf(plan.buf_gids)),

@@ -366,6 +366,20 @@ static int64_t build_table(const ColorIndex& cr, int k, OpKind kind, int t, int 
           if (pos != 0xFFFFFFFFu) h[(size_t)((int64_t)(cv * k + cu) * (int64_t)w_in + (int64_t)j)] = (uint16_t)pos;
         }
     for (size_t i = 0; i + 1 < h.size(); i += 2) tabs->push_back((uint32_t)h[i] | (uint32_t)h[i + 1] << 16);
+  } else if (kind == OP_SPMM + 900) {
+    // staged grouped SpMM: the same 16-bit positions with rows [c_v][c_u] at a pitch of
+    // whole 16-byte pieces (8 entries; 0xFFFF past the row), so a row's chunks are copied as is
+    const int p = t;
+    const uint64_t w_in = cr.nsets(p - 1);
+    const uint64_t wp = (uint64_t)spmm_staged_pitch((int64_t)w_in);
+    std::vector<uint16_t> h((size_t)(k * k * wp), 0xFFFFu);
+    for (int cv = 0; cv < k; ++cv)
+      for (int cu = 0; cu < k; ++cu)
+        for (uint64_t j = 0; j < w_in; ++j) {
+          const uint32_t pos = spmm_position(cr, k, p, cv, cu, j);
+          if (pos != 0xFFFFFFFFu) h[(size_t)((int64_t)(cv * k + cu) * (int64_t)wp + (int64_t)j)] = (uint16_t)pos;
+        }
+    for (size_t i = 0; i < h.size(); i += 2) tabs->push_back((uint32_t)h[i] | (uint32_t)h[i + 1] << 16);
   } else if (kind == OP_SPMM + 500) {
     // unpruned combine: [c_v][I_p][c_u] -> the index, in the passive table row of a
     // neighbour u of color c_u, of the p-set I_p (relative to c_v) minus c_u, or ~0
@@ -588,7 +602,8 @@ static void use_buf(Plan* P, int buf, int op) {
   P->bufs[buf].last = std::max(P->bufs[buf].last, op);
 }
 
-int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg) {
+int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg,
+                   int blocks) {
   const int64_t G = (ct + 31) / 32;
   // fewer groups than warps: each group's rounds in W / gcd(G, W) shares, so that the G * shares
   // units divide evenly among the W warps
@@ -604,7 +619,9 @@ int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, i
   if (ema_sched_rw(ld_a, ld_p, sym) >= 65535) return 0;  // every word of a row has a 16-bit index
   // at most 200 KB of the block's shared memory: under ncu a launch of this kernel that asked for
   // 218 of the 227 KB failed (the plain run of the same program did not)
-  const int64_t cap = std::min<int64_t>(smem_cap, 200 * 1024);
+  // 218 of the 227 KB failed (the plain run of the same program did not); two blocks share an SM's
+  // 228 KB less 1 KB reserved per block
+  const int64_t cap = blocks == 2 ? (smem_cap + 1024) / 2 - 1024 : std::min<int64_t>(smem_cap, 200 * 1024);
   for (int r : {8, 6, 4, 2})
     if (ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= cap) return r;
   return 0;
@@ -874,6 +891,10 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           // every SpMM of the 12-, 13- and 15-vertex trees on R-MAT 21 (narrow rows 1.4-3x faster)
           op.spmm_buckets = false;
           op.spmm_variant = op.cols_p <= 256 ? 13 : 15;
+          if (spmm_staged_fits(batch, op.cols_p, op.ld_out, elem, smem_cap_of(g), 16))
+            // rows wider than 128 columns in FP32: the staged form, with RS chunks per warp in flight
+            // (R-MAT 21, the 15-vertex tree's p = 5 SpMM: 37.7 ms against 56.2 in registers)
+            op.spmm_variant = 16;
         }
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
         if (shape == kShapeSpmmBuckets && spmm_bucket_bytes(batch, k, op.cols_p, elem) <= kSpmmBucketTuneMaxBytes) {
@@ -905,6 +926,11 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                    spmm_grouped_fits(batch, op.ld_out, elem, smem_cap_of(g))) {
           op.spmm_buckets = false;
           op.spmm_variant = shape == kShapeSpmmGrouped ? 13 : 15;
+        } else if ((shape == kShapeSpmmStaged || shape == kShapeSpmmStaged8) &&
+                   spmm_staged_fits(batch, op.cols_p, op.ld_out, elem, smem_cap_of(g),
+                                    shape == kShapeSpmmStaged ? 16 : 17)) {
+          op.spmm_buckets = false;
+          op.spmm_variant = shape == kShapeSpmmStaged ? 16 : 17;
         } else if (shape == kShapeSpmmUnrolled && spmm_unrolled_fits(batch, op.cols_p, op.ld_out)) {
           op.spmm_buckets = false;
           op.spmm_variant = 11;
@@ -928,6 +954,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_pos_bytes = 0;
         }
         op.shape = op.spmm_variant == 14   ? 0
+                   : op.spmm_variant == 17 ? kShapeSpmmStaged8
+                   : op.spmm_variant == 16 ? kShapeSpmmStaged
                    : op.spmm_variant == 15 ? kShapeSpmmGrouped8
                    : op.spmm_variant == 13 ? kShapeSpmmGrouped
                    : op.spmm_variant == 12 ? kShapeSpmmWide
@@ -954,6 +982,9 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
                                                            &P->tabs, &tcache)
                      : op.spmm_variant == 13 || op.spmm_variant == 15
                                              ? build_table(cr, k, (OpKind)(OP_SPMM + 800), Pc.size, 0, &P->tabs,
+                                                           &tcache)
+                     : op.spmm_variant == 16 || op.spmm_variant == 17
+                                             ? build_table(cr, k, (OpKind)(OP_SPMM + 900), Pc.size, 0, &P->tabs,
                                                            &tcache)
                      : op.spmm_variant == 14 ? build_table(cr, k, (OpKind)(OP_SPMM + 500), Pc.size, 0,
                                                            &P->tabs, &tcache)
@@ -1048,17 +1079,20 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       // 256 words or more (measured faster than every other form on every such combine of the 13-
       // and 15-vertex trees on R-MAT 21; slower on rows of about a hundred words)
       const bool sched_default = shape == 0 && op.ld_a + (op.ema_sym ? 0 : op.ld_p) >= 256;
-      if (!op.ema_reg_k && batch == 1 && (shape == kShapeEmaSched || sched_default)) {
+      const bool sched2 = shape == kShapeEmaSched2;
+      if (!op.ema_reg_k && batch == 1 && (shape == kShapeEmaSched || sched2 || sched_default)) {
         int upg = 1;
-        const int r = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, smem_cap, &upg);
+        const int r = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, smem_cap, &upg, sched2 ? 2 : 1);
         if (r > 0) {
           op.ema_sched = r;
           op.ema_upg = upg;
           op.ema_vrpl = 0;
         }
       }
-      op.shape = op.ema_reg_k ? kShapeEmaReg : op.ema_sched ? kShapeEmaSched : op.ema_vrpl ? 100 + op.ema_vrpl
-                                                                                          : op.ema_rows;
+      op.shape = op.ema_reg_k    ? kShapeEmaReg
+                 : op.ema_sched  ? (sched2 ? kShapeEmaSched2 : kShapeEmaSched)
+                 : op.ema_vrpl   ? 100 + op.ema_vrpl
+                                 : op.ema_rows;
       if (op.ema_sym) op.nsplit /= 2;  // C(2p, p) is even
       // the vertex-tile kernel takes the raw split indices (rows 0, no column offset)
       op.tab_off = !build_tabs ? 0
@@ -1129,7 +1163,7 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
   P->n_states = n_states;
   P->buf_states = add_buf(P, "states", 8LL * std::max(1, n_states), 0);
   bool grouped = false;
-  for (const PlanOp& op : P->ops) grouped |= op.kind == OP_SPMM && (op.spmm_variant == 13 || op.spmm_variant == 15);
+  for (const PlanOp& op : P->ops) grouped |= op.kind == OP_SPMM && spmm_variant_grouped(op.spmm_variant);
   if (grouped) {
     const int64_t nitems = (int64_t)g->n_seg + (g->n_act - g->n_heavy);
     P->buf_gids = add_buf(P, "group_ids", 4LL * batch * g->nnz, 0);
@@ -1170,6 +1204,13 @@ static bool tables_in_range(const Plan& P, int k) {
     } else if (op.kind == OP_SPMM && (op.spmm_variant == 13 || op.spmm_variant == 15)) {
       const int64_t n = (int64_t)k * k * op.cols_p;
       if ((n + 1) / 2 > left) return false;
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
+      for (int64_t i = 0; i < n; ++i)
+        if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
+    } else if (op.kind == OP_SPMM && (op.spmm_variant == 16 || op.spmm_variant == 17)) {
+      // rows of whole 16-byte pieces, copied as such: the table must start on a 16-byte boundary
+      const int64_t n = (int64_t)k * k * spmm_staged_pitch(op.cols_p);
+      if (n / 2 > left || op.tab_off % 4 != 0) return false;
       const uint16_t* h = reinterpret_cast<const uint16_t*>(t);
       for (int64_t i = 0; i < n; ++i)
         if (h[i] != 0xFFFFu && h[i] >= (uint32_t)op.cols_out) return false;
@@ -1265,6 +1306,9 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       c.push_back(kShapeSpmmGrouped);
       if (op.cols_p > 256) c.push_back(kShapeSpmmGrouped8);  // chunks of 256 columns
     }
+    if (spmm_staged_fits(P.batch, op.cols_p, op.ld_out, P.elem, smem_cap, 16)) c.push_back(kShapeSpmmStaged);
+    if (op.cols_p > 256 && spmm_staged_fits(P.batch, op.cols_p, op.ld_out, P.elem, smem_cap, 17))
+      c.push_back(kShapeSpmmStaged8);
     c.push_back(kShapeSpmmDirect);
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);
@@ -1291,8 +1335,12 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       if (ema_vertex_fits(P.batch, v, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap)) c.push_back(100 + v);
     if (P.elem == 4 && ema_reg_compiled(P.k - 1, op.a - 1, op.p, op.ema_sym)) c.push_back(kShapeEmaReg);
     int upg = 1;
-    if (P.batch == 1 && ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg) > 0)
+    if (P.batch == 1 && ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg) > 0) {
       c.insert(c.begin(), kShapeEmaSched);
+      const int r1 = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg);
+      const int r2 = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg, 2);
+      if (r2 > 0 && r2 < r1) c.insert(c.begin() + 1, kShapeEmaSched2);  // a different row count
+    }
   }
   if (c.size() < 2) c.clear();
   return c;

@@ -248,17 +248,23 @@ constexpr int kShapeSpmmDirect = 1, kShapeSpmmPrefetch = 2, kShapeSpmmBuckets = 
               kShapeSpmmPacked = 5, kShapeSpmmRing2 = 6, kShapeSpmmRing4 = 7, kShapeSpmmDirectB = 8,
               kShapeSpmmDirectBLane = 9, kShapeSpmmBucketsB = 10, kShapeSpmmDirectB8 = 11,
               kShapeSpmmDirectB12 = 12, kShapeSpmmDirectBPriv = 13, kShapeSpmmUnrolled = 14,
-              kShapeSpmmWide = 15, kShapeSpmmGrouped = 16, kShapeSpmmGrouped8 = 17;
+              kShapeSpmmWide = 15, kShapeSpmmGrouped = 16, kShapeSpmmGrouped8 = 17, kShapeSpmmStaged = 18,
+              kShapeSpmmStaged8 = 19;
 // private accumulator columns (shape 13) are tried while a warp's fit in this
 constexpr int64_t kSpmmPrivMaxBytes = 16 * 1024;
 constexpr int64_t kSpmmPackedMaxBytes = 24 * 1024;
 // eMA shape codes for the vertex-tile kernel (1 or 2 rows per lane) and the
 // register form (FP32, the (K, a-1, p, symmetric) shapes compiled in)
-constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103, kShapeEmaSched = 104;
+constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103, kShapeEmaSched = 104,
+              kShapeEmaSched2 = 105;
 // the scheduled eMA (shape 104, one coloring per pass, kEmaSchedWarps warps per block): rows a block
 // stages (8, 6, 4 or 2 within 200 KB; 0 = does not fit) and shares of each group of 32 outputs' rounds
 constexpr int kEmaSchedWarps = 16;
-int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg);
+// rows per block of the scheduled eMA: the most of 8, 6, 4, 2 whose block fits in at most 200 KB
+// (blocks = 1) or in half of an SM's shared memory (blocks = 2: two blocks per SM, one staging its
+// rows while the other computes); 0 when none fits
+int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg,
+                   int blocks = 1);
 // words of one staged row: M_a row, P row (unless the table is combined with itself), 4 zero words
 inline int64_t ema_sched_rw(int64_t ld_a, int64_t ld_p, bool sym) { return ld_a + (sym ? 0 : ld_p) + 4; }
 inline int64_t ema_sched_smem(int rows, int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int upg) {
@@ -292,6 +298,30 @@ inline bool spmm_unrolled_fits(int batch, int64_t w_in, int64_t ld_out) {
 // bits, and at least two warps' output rows in shared memory
 inline bool spmm_grouped_fits(int batch, int64_t ld_out, int elem, int64_t smem_cap) {
   return batch <= 4 && ld_out < 65535 && 2 * ld_out * elem <= smem_cap;
+}
+// the grouped SpMM's kernel variants: 13 and 15 (neighbour rows in registers, chunks of 512 or
+// 256 columns), 16 and 17 (the staged form: rows copied into a ring of shared-memory slots)
+inline bool spmm_variant_grouped(int v) { return v == 13 || v == 15 || v == 16 || v == 17; }
+// the staged form: chunks of 128 nr4 columns (the fewest chunks, at most 1,024 columns for
+// variant 16 and 512 for 17), a ring of 4 (16) or 8 (17) chunk slots per warp, and rows of
+// 16-bit positions at a pitch of whole 16-byte pieces
+inline int spmm_staged_nr4(int64_t w_in, int variant) {
+  const int cap = variant == 17 ? 4 : 8;
+  const int n = w_in <= 256 ? 2 : w_in <= 512 ? 4 : 8;
+  return n < cap ? n : cap;
+}
+inline int spmm_staged_rs(int variant) { return variant == 17 ? 8 : 4; }
+inline int64_t spmm_staged_pitch(int64_t w_in) { return (w_in + 7) / 8 * 8; }
+// a warp's shared memory: its output row, the chunk ring, rs + 1 position chunks, rs colors
+inline int64_t spmm_staged_warp_bytes(int64_t w_in, int64_t ld_out, int variant) {
+  const int64_t ch = 128 * spmm_staged_nr4(w_in, variant), rs = spmm_staged_rs(variant);
+  return 4 * (ld_out + rs * ch + (rs + 1) * ch / 2 + (rs + 3) / 4 * 4);
+}
+// whether the staged form takes this op: FP32, one coloring per pass, rows wider than 128
+// columns, positions in 16 bits, and at least two warps in shared memory
+inline bool spmm_staged_fits(int batch, int64_t w_in, int64_t ld_out, int elem, int64_t smem_cap, int variant) {
+  return batch == 1 && elem == 4 && w_in > 128 && ld_out < 65535 &&
+         2 * spmm_staged_warp_bytes(w_in, ld_out, variant) <= smem_cap;
 }
 // entries per [c_v][c_u] row of the packed position table (rows of whole words)
 inline int64_t spmm_packed_ld(int64_t w_in, int eb) { return (w_in * eb + 3) / 4 * 4 / eb; }

@@ -87,8 +87,9 @@ def test_wide_shapes_match_oracle(c3, shape):
 
 
 def test_scheduled_ema_matches_oracle(c3):
-    # the scheduled eMA (bank-conflict-free rounds, rows staged by bulk copies) on the 13- and 15-vertex
-    # trees' wide combines, one coloring per pass
+    # the scheduled eMA (bank-conflict-free rounds, rows staged by bulk copies; with up to 8 rows per
+    # block, and with half as many so that two blocks share an SM) on the 13- and 15-vertex trees'
+    # wide combines, one coloring per pass
     gold, g = c3
     for name in ("pruefer13", "pruefer15"):
         rec = gold["templates"][name]
@@ -96,5 +97,20 @@ def test_scheduled_ema_matches_oracle(c3):
         seeds = np.array(gold["seeds"][:2], dtype=np.uint64)
         want = np.array([float(int(r["maps"])) for r in rec["results"][:2]])
         for precision, tol in (("fp32", 1e-5), ("fp64", 1e-12)):
-            r = sgc.count(g, t, seeds, precision=precision, batch=1, ema_rows=104)
-            assert np.allclose(r.maps, want, rtol=tol, atol=0), (name, precision, r.maps, want)
+            for shape in (104, 105):
+                r = sgc.count(g, t, seeds, precision=precision, batch=1, ema_rows=shape)
+                assert np.allclose(r.maps, want, rtol=tol, atol=0), (name, precision, shape, r.maps, want)
+
+
+@pytest.mark.parametrize("shape", [18, 19])
+def test_staged_spmm_matches_oracle(c3, shape):
+    # the grouped SpMM with neighbour rows copied into shared-memory rings (one coloring per pass) on
+    # all three templates' SpMMs wider than 128 columns; narrower ones keep the planner's shapes
+    gold, g = c3
+    for name in NAMES:
+        rec = gold["templates"][name]
+        t = sgc.Template(parent_of(rec["spec"]))
+        seeds = np.array(gold["seeds"][:2], dtype=np.uint64)
+        want = np.array([float(int(r["maps"])) for r in rec["results"][:2]])
+        r = sgc.count(g, t, seeds, precision="fp32", batch=1, spmm_shape=shape)
+        assert np.allclose(r.maps, want, rtol=1e-5, atol=0), (name, shape, r.maps, want)

@@ -132,6 +132,28 @@ def test_grouped_spmm(batch, precision):
         check(a.maps[: len(few)], oracle_maps(rp, ci, parent, few), precision)
 
 
+def test_staged_spmm_sums_in_the_same_order():
+    # neighbour rows and output positions copied into shared-memory rings by asynchronous copies:
+    # with the register form's chunk widths (shape 19: 512 columns; shape 18 up to 512-column rows)
+    # the same sums in the same order, so FP32 maps equal the register form's bit for bit; shape 18's
+    # 1,024-column chunks group a position's terms differently.  Rows of 165 to 2,002 columns (one
+    # to four chunks), heavy-row segments, rows whose neighbours all share their color, the oracle.
+    sgc.build()
+    rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=6)
+    g = sgc.Graph(rp, ci)
+    assert g.stats()["n_heavy"] > 0
+    for parent in (sgcgen.path_tree(12), sgcgen.pruefer_tree(13, 7), sgcgen.pruefer_tree(15, 9)):
+        t = sgc.Template(parent)
+        seeds = np.arange(40, 43, dtype=np.uint64)
+        a = sgc.count(g, t, seeds, precision="fp32", spmm_shape=16, batch=1)
+        b = sgc.count(g, t, seeds, precision="fp32", spmm_shape=19, batch=1)
+        c = sgc.count(g, t, seeds, precision="fp32", spmm_shape=18, batch=1)
+        assert np.array_equal(a.maps, b.maps)
+        assert np.allclose(a.maps, c.maps, rtol=1e-6, atol=0)
+        if len(parent) <= 13:
+            check(c.maps[:1], oracle_maps(rp, ci, parent, seeds[:1]), "fp32")
+
+
 @pytest.mark.parametrize("batch", [1, 4, 8, 32])
 def test_wide_spmm_sums_in_the_same_order(batch):
     # 16-bit positions in chunks of eight: FP32 maps equal the batch-specialised direct form's bit
@@ -169,7 +191,7 @@ def test_unrolled_spmm_sums_in_the_same_order(batch):
         check(b.maps, oracle_maps(rp, ci, parent, seeds), "fp32")
 
 
-@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102, 103, 104])
+@pytest.mark.parametrize("ema_rows", [64, 32, 16, 8, 4, 2, 1, 101, 102, 103, 104, 105])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_ema_shape(ema_rows, precision):
     sgc.build()
@@ -177,8 +199,9 @@ def test_every_ema_shape(ema_rows, precision):
     g = sgc.Graph(rp, ci)
     # the spider's eMA is symmetric (a table with itself), the others are not;
     # vertex tiles need 4..32 colorings per pass: 16 + 8 + 1 exercises both kernels;
-    # the scheduled form (104) takes one coloring per pass, tiles of 8 rows with a ragged last one
-    batch = 1 if ema_rows == 104 else 16
+    # the scheduled forms (104, 105: half the rows, two blocks per SM) take one coloring per pass,
+    # tiles of up to 8 rows with a ragged last one
+    batch = 1 if ema_rows in (104, 105) else 16
     for parent in (sgcgen.pruefer_tree(9, 1009), sgcgen.path_tree(8), sgcgen.spider_tree([3, 3, 3]),
                    sgcgen.pruefer_tree(13, 7)):
         t = sgc.Template(parent)
