@@ -95,9 +95,9 @@ typedef struct sgc_options {
                           coloring sums the rows of each neighbour color in registers and adds each
                           color's sum into the output row once; columns in chunks of up to 512),
                           17 grouped in chunks of up to 256 columns, 18 grouped with the
-                          neighbour rows copied into a ring of 4 shared-memory chunks of up to
+                          neighbour rows copied into a ring of 3 shared-memory chunks of up to
                           1,024 columns per warp (FP32, one coloring per pass, rows wider than 128
-                          columns), 19 the same with a ring of 8 chunks of up to 512 columns; ops
+                          columns), 19 the same with a ring of 2 chunks (more warps per SM); ops
                           it does not fit keep theirs.  0 (default) = planner or
                           autotuner.  Results do not depend on it beyond FP32 summation order. */
   int32_t ema_rows;    /* force the eMA shape: 64, 32, 16, 8, 4, 2 or 1 rows staged column-major per

@@ -255,7 +255,7 @@ SHAPE_NAMES = {1: "direct", 2: "direct+prefetch", 3: "buckets", 4: "register-buc
                9: "direct-batch+lane-table", 10: "buckets-batch", 11: "direct-batch-g8", 12: "direct-batch-g12",
                13: "direct-batch-private", 14: "direct-batch-unrolled", 15: "direct-batch-wide",
                16: "grouped", 17: "grouped-256",
-               18: "grouped-staged", 19: "grouped-staged-8"}
+               18: "grouped-staged", 19: "grouped-staged-2"}
 
 
 def sgc_autotune(g: int, t: int, opt: sgc_options | None = None) -> list:

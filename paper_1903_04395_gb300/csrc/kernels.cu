@@ -1333,14 +1333,19 @@ __global__ void __launch_bounds__(kBlock) k_spmm_g(
       T a[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) a[r] = T(0);
+      // a group's positions are distinct (one to one from a neighbour's columns), so all of a
+      // lane's output words are read before any is written
       auto flush = [&](int c) {
         const uint16_t* tp = tv + (int64_t)c * w_in + jl;
+        uint32_t pk[NR];
+        T old[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) pk[r] = jl + 32 * r < w_in ? (uint32_t)__ldg(tp + 32 * r) : 0xFFFFu;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) old[r] = pk[r] != 0xFFFFu ? acc[pk[r]] : T(0);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          if (jl + 32 * r < w_in) {
-            const uint32_t pos = __ldg(tp + 32 * r);
-            if (pos != 0xFFFFu) acc[pos] += a[r];
-          }
+          if (pk[r] != 0xFFFFu) acc[pk[r]] = old[r] + a[r];
           a[r] = T(0);
         }
         __syncwarp();
@@ -1405,7 +1410,9 @@ __global__ void __launch_bounds__(kBlock) k_spmm_g(
 // at most RS groups ahead, so they never overwrite the group being summed.
 // Every step commits one copy group (an empty one once the sequence is used
 // up): the entry at the head has landed when all but the newest RS - 1 groups
-// are done.  Lane l sums the columns j0 + 128 r + 4 l + q (r < NR4, q < 4).
+// are done.  The entries' colors, known to every lane when they are issued,
+// wait in a register queue of RS.  Lane l sums the columns j0 + 128 r + 4 l + q
+// (r < NR4, q < 4).
 // Per position the sums run in k_spmm_g's order (CSR order within a color,
 // colors ascending): the same results.
 template <int NR4, int RS>
@@ -1422,12 +1429,11 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
-  // a warp's words: its output row, RS row chunks, PB chunks of 16-bit positions, RS group colors
-  const int64_t per_warp = (int64_t)ld_out + RS * CH + PB * CH / 2 + (RS + 3) / 4 * 4;
+  // a warp's words: its output row, RS row chunks, PB chunks of 16-bit positions
+  const int64_t per_warp = (int64_t)ld_out + RS * CH + PB * CH / 2;
   float* acc = reinterpret_cast<float*>(sm_raw) + warp * per_warp;
   float* slots = acc + ld_out;
   uint16_t* pbufs = reinterpret_cast<uint16_t*>(slots + RS * CH);
-  int* slot_c = reinterpret_cast<int*>(slots + RS * CH + PB * CH / 2);
   const int64_t nitems = (int64_t)n_seg + (n_act - n_heavy);
   const int64_t S = (int64_t)gridDim.x * wpb;
   const int nch = (w_in + CH - 1) / CH;
@@ -1452,7 +1458,9 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
     }
     return w;
   };
-  auto issue = [&](int slot) {
+  // copies the sequence's next entry into `slot` and returns its color (-1 past the end)
+  auto issue = [&](int slot) -> int {
+    int c = -1;
     if (lw < nitems) {
       const int blk = le >> 5;
       if (blk != lblk) {
@@ -1462,7 +1470,7 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
         lblk = blk;
       }
       const int32_t u = __shfl_sync(full, lid, le & 31);
-      const int c = __shfl_sync(full, lcol, le & 31);
+      c = __shfl_sync(full, lcol, le & 31);
       const int j0 = lc * CH;
       const int nv = (min(CH, w_in - j0) + 3) >> 2;  // 16-byte pieces of the row chunk
       const float* src = Min + (int64_t)u * ld_in + j0;
@@ -1480,7 +1488,6 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
         lpb = lpb + 1 == PB ? 0 : lpb + 1;
         lprev = c;
       }
-      if (lane == 0) slot_c[slot] = c;
       if (++le == lkept) {
         le = 0;
         lprev = -1;
@@ -1491,10 +1498,14 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
       }
     }
     cp_async_commit();
+    return c;
   };
 
+  // the colors of the RS entries in flight, oldest first (every lane holds them)
+  int cq[RS];
   lw = seek(lw);
-  for (int i = 0; i < RS; ++i) issue(i);
+#pragma unroll
+  for (int i = 0; i < RS; ++i) cq[i] = issue(i);
   float m = 0.f;
   int slot = 0, cpb = 0;
   for (int64_t w = (int64_t)blockIdx.x * wpb + warp; w < nitems; w += S) {
@@ -1510,41 +1521,66 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
       for (int r = 0; r < NR4; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       int cur = -1;
       const uint16_t* pos = pbufs;
+      // a group's positions are distinct (the map from a neighbour's columns to v's is one to
+      // one), so a lane's output words are read before any is written: one shared-memory round
+      // trip per 8 or 16 words instead of one per word (the positions and old values of all 4 NR4
+      // words would not fit in registers beside the sums and the next chunk's words)
       auto flush = [&]() {
+        constexpr int RB = NR4 == 8 ? 2 : NR4 < 4 ? NR4 : 4;  // 8 or 16 words at a time
 #pragma unroll
-        for (int r = 0; r < NR4; ++r) {
-          const int jb = j0 + 128 * r + 4 * lane;
-          const uint2 pw = *reinterpret_cast<const uint2*>(pos + 128 * r + 4 * lane);
-          const uint32_t p4[4] = {pw.x & 0xffffu, pw.x >> 16, pw.y & 0xffffu, pw.y >> 16};
+        for (int r0 = 0; r0 < NR4; r0 += RB) {
+          uint32_t pk[RB][4];
+          float old[RB][4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (jb + q < w_in && p4[q] != 0xFFFFu) acc[p4[q]] += a[r][q];
-            a[r][q] = 0.f;
+          for (int i = 0; i < RB; ++i) {
+            const int r = r0 + i, jb = j0 + 128 * r + 4 * lane;
+            const uint2 pw = *reinterpret_cast<const uint2*>(pos + 128 * r + 4 * lane);
+            pk[i][0] = jb < w_in ? pw.x & 0xffffu : 0xFFFFu;
+            pk[i][1] = jb + 1 < w_in ? pw.x >> 16 : 0xFFFFu;
+            pk[i][2] = jb + 2 < w_in ? pw.y & 0xffffu : 0xFFFFu;
+            pk[i][3] = jb + 3 < w_in ? pw.y >> 16 : 0xFFFFu;
           }
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) old[i][q] = pk[i][q] != 0xFFFFu ? acc[pk[i][q]] : 0.f;
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (pk[i][q] != 0xFFFFu) acc[pk[i][q]] = old[i][q] + a[r0 + i][q];
+              a[r0 + i][q] = 0.f;
+            }
         }
         __syncwarp();
       };
       for (int e = 0; e < kept; ++e) {
         cp_async_wait<RS - 1>();
         __syncwarp();
-        const int c = slot_c[slot];
+        const int c = cq[0];
+        // the entry's chunk is read before a group ends, so its loads overlap the flush
+        const float4* s4 = reinterpret_cast<const float4*>(slots + slot * CH) + lane;
+        float4 x[NR4];
+#pragma unroll
+        for (int r = 0; r < NR4; ++r) x[r] = s4[32 * r];
         if (c != cur) {
           if (cur >= 0) flush();
           cur = c;
           pos = pbufs + cpb * CH;
           cpb = cpb + 1 == PB ? 0 : cpb + 1;
         }
-        const float4* s4 = reinterpret_cast<const float4*>(slots + slot * CH) + lane;
 #pragma unroll
         for (int r = 0; r < NR4; ++r) {
-          const float4 x = s4[32 * r];
-          a[r][0] += x.x;
-          a[r][1] += x.y;
-          a[r][2] += x.z;
-          a[r][3] += x.w;
+          a[r][0] += x[r].x;
+          a[r][1] += x[r].y;
+          a[r][2] += x[r].z;
+          a[r][3] += x[r].w;
         }
         __syncwarp();
-        issue(slot);
+        const int cn = issue(slot);
+#pragma unroll
+        for (int i = 0; i + 1 < RS; ++i) cq[i] = cq[i + 1];
+        cq[RS - 1] = cn;
         slot = slot + 1 == RS ? 0 : slot + 1;
       }
       if (cur >= 0) flush();
@@ -2208,8 +2244,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_final_reg(const T* __restrict__ M
   }
 }
 
-// the (K, p) shapes of the last step compiled in: the 10-color spider's
-#define SGC_FINAL_REG_SHAPES(X) X(9, 3)
+// the (K, p) shapes of the last step compiled in: the 10-color spider's, the 7-, 8-, 9- and
+// 11-vertex Pruefer trees' and the 15-vertex one's (the 10-vertex tree's (9, 5), 126 terms per
+// row, spills registers and keeps the table form)
+#define SGC_FINAL_REG_SHAPES(X) \
+  X(9, 3) X(6, 1) X(7, 3) X(8, 4) X(10, 2) X(14, 1) X(14, 13)
 
 // The symmetric register-form eMA fused with the last step that consumes it:
 // the root's table T(v, .) = sum over splits of P(v, A) P(v, S - A) (as in
@@ -2842,13 +2881,14 @@ sgc_status launch_spmm_grouped(const sgc_graph* g, const Plan& plan, const PlanO
                                                       gcols, gkept, M, (int)op.cols_p, (int)op.ld_p, P,      \
                                                       (int)op.ld_out, scratch, tab16, wpitch, si, so);       \
   } while (0)
-      if (rs == 8) {
-        if (nr4 == 2) SGC_GS(2, 8);
-        else SGC_GS(4, 8);
+      if (rs == 2) {
+        if (nr4 == 2) SGC_GS(2, 2);
+        else if (nr4 == 4) SGC_GS(4, 2);
+        else SGC_GS(8, 2);
       } else {
-        if (nr4 == 2) SGC_GS(2, 4);
-        else if (nr4 == 4) SGC_GS(4, 4);
-        else SGC_GS(8, 4);
+        if (nr4 == 2) SGC_GS(2, 3);
+        else if (nr4 == 4) SGC_GS(4, 3);
+        else SGC_GS(8, 3);
       }
 #undef SGC_GS
       ++*nk;

@@ -892,8 +892,8 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
           op.spmm_buckets = false;
           op.spmm_variant = op.cols_p <= 256 ? 13 : 15;
           if (spmm_staged_fits(batch, op.cols_p, op.ld_out, elem, smem_cap_of(g), 16))
-            // rows wider than 128 columns in FP32: the staged form, with RS chunks per warp in flight
-            // (R-MAT 21, the 15-vertex tree's p = 5 SpMM: 37.7 ms against 56.2 in registers)
+            // rows wider than 128 columns in FP32: the staged form, with 3 chunks per warp in flight
+            // (R-MAT 21, the 15-vertex tree's p = 5 SpMM: 31.8 ms against 37.6 in registers)
             op.spmm_variant = 16;
         }
         const int shape = shapes && idx < (int)shapes->size() ? (*shapes)[idx] : 0;
@@ -1307,8 +1307,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       if (op.cols_p > 256) c.push_back(kShapeSpmmGrouped8);  // chunks of 256 columns
     }
     if (spmm_staged_fits(P.batch, op.cols_p, op.ld_out, P.elem, smem_cap, 16)) c.push_back(kShapeSpmmStaged);
-    if (op.cols_p > 256 && spmm_staged_fits(P.batch, op.cols_p, op.ld_out, P.elem, smem_cap, 17))
-      c.push_back(kShapeSpmmStaged8);
+    if (spmm_staged_fits(P.batch, op.cols_p, op.ld_out, P.elem, smem_cap, 17)) c.push_back(kShapeSpmmStaged8);
     c.push_back(kShapeSpmmDirect);
     c.push_back(kShapeSpmmDirectB);
     if (op.ld_out < 65535) c.push_back(kShapeSpmmDirectBLane);

@@ -302,20 +302,19 @@ inline bool spmm_grouped_fits(int batch, int64_t ld_out, int elem, int64_t smem_
 // the grouped SpMM's kernel variants: 13 and 15 (neighbour rows in registers, chunks of 512 or
 // 256 columns), 16 and 17 (the staged form: rows copied into a ring of shared-memory slots)
 inline bool spmm_variant_grouped(int v) { return v == 13 || v == 15 || v == 16 || v == 17; }
-// the staged form: chunks of 128 nr4 columns (the fewest chunks, at most 1,024 columns for
-// variant 16 and 512 for 17), a ring of 4 (16) or 8 (17) chunk slots per warp, and rows of
-// 16-bit positions at a pitch of whole 16-byte pieces
+// the staged form: chunks of 128 nr4 columns (the fewest chunks, at most 1,024 columns), a ring
+// of 3 (variant 16) or 2 (17: less shared memory per warp, more warps per SM) chunk slots per
+// warp, and rows of 16-bit positions at a pitch of whole 16-byte pieces
 inline int spmm_staged_nr4(int64_t w_in, int variant) {
-  const int cap = variant == 17 ? 4 : 8;
-  const int n = w_in <= 256 ? 2 : w_in <= 512 ? 4 : 8;
-  return n < cap ? n : cap;
+  (void)variant;
+  return w_in <= 256 ? 2 : w_in <= 512 ? 4 : 8;
 }
-inline int spmm_staged_rs(int variant) { return variant == 17 ? 8 : 4; }
+inline int spmm_staged_rs(int variant) { return variant == 17 ? 2 : 3; }
 inline int64_t spmm_staged_pitch(int64_t w_in) { return (w_in + 7) / 8 * 8; }
-// a warp's shared memory: its output row, the chunk ring, rs + 1 position chunks, rs colors
+// a warp's shared memory: its output row, the chunk ring, rs + 1 chunks of positions
 inline int64_t spmm_staged_warp_bytes(int64_t w_in, int64_t ld_out, int variant) {
   const int64_t ch = 128 * spmm_staged_nr4(w_in, variant), rs = spmm_staged_rs(variant);
-  return 4 * (ld_out + rs * ch + (rs + 1) * ch / 2 + (rs + 3) / 4 * 4);
+  return 4 * (ld_out + rs * ch + (rs + 1) * ch / 2);
 }
 // whether the staged form takes this op: FP32, one coloring per pass, rows wider than 128
 // columns, positions in 16 bits, and at least two warps in shared memory

@@ -134,10 +134,11 @@ def test_grouped_spmm(batch, precision):
 
 def test_staged_spmm_sums_in_the_same_order():
     # neighbour rows and output positions copied into shared-memory rings by asynchronous copies:
-    # with the register form's chunk widths (shape 19: 512 columns; shape 18 up to 512-column rows)
-    # the same sums in the same order, so FP32 maps equal the register form's bit for bit; shape 18's
-    # 1,024-column chunks group a position's terms differently.  Rows of 165 to 2,002 columns (one
-    # to four chunks), heavy-row segments, rows whose neighbours all share their color, the oracle.
+    # the ring's depth (shape 18: 3 chunks, 19: 2) does not change the sums, so their FP32 maps are
+    # equal bit for bit; against the register form (512-column chunks) rows of up to 512 columns sum
+    # in the same order and 1,024-column chunks group a position's terms differently.  Rows of 165
+    # to 2,002 columns (one or two chunks), heavy-row segments, rows whose neighbours all share
+    # their color, the oracle.
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=6)
     g = sgc.Graph(rp, ci)
@@ -148,7 +149,7 @@ def test_staged_spmm_sums_in_the_same_order():
         a = sgc.count(g, t, seeds, precision="fp32", spmm_shape=16, batch=1)
         b = sgc.count(g, t, seeds, precision="fp32", spmm_shape=19, batch=1)
         c = sgc.count(g, t, seeds, precision="fp32", spmm_shape=18, batch=1)
-        assert np.array_equal(a.maps, b.maps)
+        assert np.array_equal(b.maps, c.maps)
         assert np.allclose(a.maps, c.maps, rtol=1e-6, atol=0)
         if len(parent) <= 13:
             check(c.maps[:1], oracle_maps(rp, ci, parent, seeds[:1]), "fp32")
@@ -260,14 +261,25 @@ def test_fused_combine_and_last_step(monkeypatch):
         check(fused.maps, oracle_maps(rp, ci, parent, seeds), "fp32")
 
 
+FINAL_SHAPE_TREES = {  # template -> the last step's (K, p) on R-MAT 13 (seed 12) with the planner's root
+    "spider10": (sgcgen.spider_tree([3, 3, 3]), (9, 3)),
+    "pruefer7": (sgcgen.pruefer_tree(7, 1007), (6, 1)),
+    "pruefer8": (sgcgen.pruefer_tree(8, 1008), (7, 3)),
+    "pruefer9": (sgcgen.pruefer_tree(9, 1009), (8, 4)),
+    "pruefer11": (sgcgen.pruefer_tree(11, 1011), (10, 2)),
+    "pruefer15": (sgcgen.pruefer_tree(15, 9), (14, 1)),
+}
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_final_compile_time_form_matches_table_form(monkeypatch, precision):
-    # the last step with compile-time complement indices (the spider's k = 10, p = 3 shape) sums
-    # every row in the table-driven kernel's order: identical maps in either precision
+@pytest.mark.parametrize("name", list(FINAL_SHAPE_TREES))
+def test_final_compile_time_form_matches_table_form(monkeypatch, precision, name):
+    # the last step with compile-time complement indices sums every row in the table-driven
+    # kernel's order: identical maps in either precision, for each (K, p) shape compiled in
     sgc.build()
     rp, ci = sgcgen.rmat(13, edge_factor=8, a=0.57, b=0.19, c=0.19, seed=12)
-    parent = sgcgen.spider_tree([3, 3, 3])
-    seeds = np.arange(90, 101, dtype=np.uint64)
+    parent, _ = FINAL_SHAPE_TREES[name]
+    seeds = np.arange(90, 101 if len(parent) < 12 else 92, dtype=np.uint64)
     monkeypatch.setenv("SGC_NO_FUSE", "1")  # the last step as its own kernel
     got = sgc.count(sgc.Graph(rp, ci), sgc.Template(parent), seeds, precision=precision)
     monkeypatch.setenv("SGC_FINAL_TABLE", "1")
