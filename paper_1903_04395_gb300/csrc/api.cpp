@@ -220,8 +220,15 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
   for (const PlanOp& op : p1.ops)
     if (op.kind == OP_SPMM) widest = std::max<int64_t>(widest, op.ld_out * p1.elem);
   while (bmax > 1 && widest * bmax > kSpmmRowBytesPerWarp) bmax /= 2;
+  // one coloring per pass by default where the staged SpMM takes an op of more than 256 columns
+  // (R-MAT 21: the 12-vertex path at 39 ms per coloring against 58 at 4 per pass, the 13-vertex
+  // tree 59 against 83 at 2; the autotuner still measures the larger batches)
+  bool one = false;
+  for (const PlanOp& op : p1.ops)
+    one |= op.kind == OP_SPMM && (op.spmm_variant == 16 || op.spmm_variant == 17) && op.cols_p > 256;
   set->by_batch[1] = std::move(p1);
   set->bfit = 1;
+  set->btop = 1;
   for (int b = 2; b <= bmax; b *= 2) {
     Plan pb;
     rc = make_plan(g, t, o.precision, root, policy, b, true, &pb, nullptr, o.colors, o.unpruned);
@@ -233,7 +240,8 @@ sgc_status plan_batches(const sgc_graph* g, const sgc_template* t, const sgc_opt
     }
     if (pb.ws_bytes > mem_limit) break;
     set->by_batch[b] = std::move(pb);
-    set->bfit = b;
+    set->btop = b;
+    if (!one) set->bfit = b;
   }
   for (auto& kv : g->plan_cache)
     if (kv.first == key) {
@@ -313,12 +321,12 @@ sgc_status tune_plans(const sgc_graph* g, const sgc_template* t, const sgc_optio
                       DevicePool& pool, cudaStream_t st) {
   SGC_TRACE_SCOPE("autotune");
   // the largest batch and up to two halvings: wide rows favour smaller batches
-  std::vector<int> batches{set->bfit};
-  for (int b = set->bfit / 2; b >= 1 && batches.size() < 3 && set->by_batch.count(b); b /= 2) batches.push_back(b);
+  std::vector<int> batches{set->btop};
+  for (int b = set->btop / 2; b >= 1 && batches.size() < 3 && set->by_batch.count(b); b /= 2) batches.push_back(b);
   std::vector<sgc_tune_entry> report;
   sgc_tune_entry bt{};
   bt.kind = -1;
-  int best_b = set->bfit;
+  int best_b = set->btop;
   double best_per = 0;
   for (int b : batches) {
     const Plan& base = set->by_batch.at(b);

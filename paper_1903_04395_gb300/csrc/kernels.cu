@@ -33,6 +33,8 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -2421,9 +2423,23 @@ __global__ void k_final_sum(const double* __restrict__ partials, int nblocks, in
   out[b] = s;
 }
 
+// A kernel's limit on dynamic shared memory only ever grows, per device: one kernel serves ops of
+// different sizes, and a launch recorded into a CUDA graph with a larger size must not find the
+// limit lowered by a later, smaller launch (a profiler that replays graph nodes one by one
+// checks each node against the kernel's limit at that time).
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_limit;
+
 template <typename KernelT>
 void allow_smem(KernelT kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  size_t& cur = g_smem_limit[{dev, reinterpret_cast<const void*>(kernel)}];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    cur = bytes;
 }
 
 int grid_for(int64_t work, int per_block, int cap) {

@@ -375,10 +375,11 @@ inline int64_t spmm_bucket_bytes(int batch, int k, int64_t w_in, int elem) {
 constexpr int64_t kSpmmBucketMaxBytes = 4 * 1024;  // keeps ~48 warps per SM resident
 constexpr int64_t kSpmmRowBytesPerWarp = 8 * 1024;  // batch cap for wide SpMM output rows
 
-// Plans for the powers of two up to `bfit` colorings per pass (same root and
-// cut order), cached per graph.
+// Plans for the powers of two up to `btop` colorings per pass (same root and
+// cut order), cached per graph; `bfit` is the one count calls use.
 struct PlanSet {
   std::map<int, Plan> by_batch;
+  int btop = 1;  // the most colorings per pass that fit (the autotuner starts there)
   int bfit = 1;
   bool tuned = false;                 // by_batch[bfit] (and the next smaller) carry timed shapes
   std::vector<sgc_tune_entry> report; // what the autotuner measured
