@@ -1446,15 +1446,40 @@ __global__ void __launch_bounds__(512) k_spmm_gs(
   int lc = 0, le = 0, lkept = 0, llo = 0, lcv = 0, lblk = -1, lprev = -1, lpb = 0;
   int32_t lid = 0;
   int lcol = 0;
+  // the next item's kept count, first entry and row color, loaded when the copies enter an item
+  // (independent loads, in flight while that item's rows are copied)
+  int64_t nw = -1;
+  int nk = 0, nlo = 0, ncv = 0;
+  auto fetch = [&](int64_t w) {
+    nw = w;
+    if (w < nitems) {
+      nk = gkept[w];
+      const SpmmItem it = spmm_item(w, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+      nlo = it.lo;
+      ncv = colors[it.row];
+    }
+  };
   auto seek = [&](int64_t w) -> int64_t {  // the first item from w on with kept entries
     for (; w < nitems; w += S) {
-      const int kk = gkept[w];
+      int kk, lo = 0, cv = 0;
+      if (w == nw) {
+        kk = nk;
+        lo = nlo;
+        cv = ncv;
+      } else {
+        kk = gkept[w];
+        if (kk > 0) {
+          const SpmmItem it = spmm_item(w, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
+          lo = it.lo;
+          cv = colors[it.row];
+        }
+      }
       if (kk > 0) {
-        const SpmmItem it = spmm_item(w, n_seg, seg_row, seg_lo, seg_hi, n_heavy, row_ptr);
         lkept = kk;
-        llo = it.lo;
-        lcv = colors[it.row];
+        llo = lo;
+        lcv = cv;
         lblk = -1;
+        fetch(w + S);
         break;
       }
     }
