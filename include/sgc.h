@@ -108,8 +108,10 @@ typedef struct sgc_options {
                           rows; the default where it applies at 8 or more colorings per pass), or
                           104 = scheduled (one coloring per pass: up to 8 rows staged by bulk copies
                           in at most 200 KB, each output's split terms in rounds that read distinct
-                          shared-memory banks), or 105 = scheduled with half as many rows, so that
-                          two blocks share an SM (one stages its rows while the other computes);
+                          shared-memory banks), or 105 = scheduled with up to 12 rows in half of
+                          an SM's shared memory, so that two blocks share an SM (one stages its
+                          rows while the other computes; the default where each block gets at least
+                          as many rows as one block alone would);
                           ops it does not fit keep theirs; 0 (default) = planner or autotuner */
   int32_t colors;      /* number of colors k (Section 2.1: k >= |T|): 0 (default) = |T|, else
                           |T| <= colors <= SGC_MAX_K.  A map is colorful when its |T| images have

@@ -2804,6 +2804,7 @@ sgc_status launch_ema(const PlanOp& op, const T* Ma, const T* P, T* out, const u
   if (op.ema_sched > 0) {
     if (lb != 0) return fail(SGC_ERR_INTERNAL, "the scheduled eMA takes one coloring per pass");
     switch (op.ema_sched) {
+      case 12: return launch_ema_s<T, 12>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
       case 8: return launch_ema_s<T, 8>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
       case 6: return launch_ema_s<T, 6>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);
       case 4: return launch_ema_s<T, 4>(op, Ma, P, out, tab, rows, sa, sp, so, smem_cap, st);

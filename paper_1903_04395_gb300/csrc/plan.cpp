@@ -617,13 +617,14 @@ int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, i
   }
   *upg = G < W ? (int)(W / gcd) : 1;
   if (ema_sched_rw(ld_a, ld_p, sym) >= 65535) return 0;  // every word of a row has a 16-bit index
-  // at most 200 KB of the block's shared memory: under ncu a launch of this kernel that asked for
-  // 218 of the 227 KB failed (the plain run of the same program did not)
-  // 218 of the 227 KB failed (the plain run of the same program did not); two blocks share an SM's
-  // 228 KB less 1 KB reserved per block
+  // at most 200 KB of the block's shared memory (under ncu a launch of this kernel that asked for
+  // 218 of the 227 KB failed; the plain run of the same program did not); two blocks share an
+  // SM's 228 KB less 1 KB reserved per block, and take up to 12 rows each (the 15-vertex tree's
+  // (8, 3, 5) combine on R-MAT 21: 25.7 ms at 12 rows and two blocks, 27.5 at 8 rows and one
+  // block, 28.1 at 16 rows and one block)
   const int64_t cap = blocks == 2 ? (smem_cap + 1024) / 2 - 1024 : std::min<int64_t>(smem_cap, 200 * 1024);
-  for (int r : {8, 6, 4, 2})
-    if (ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= cap) return r;
+  for (int r : {12, 8, 6, 4, 2})
+    if ((blocks == 2 || r <= 8) && ema_sched_smem(r, ct, ld_a, ld_p, sym, elem, *upg) <= cap) return r;
   return 0;
 }
 
@@ -1079,7 +1080,13 @@ static void plan_for(const sgc_graph* g, const sgc_template* t, int precision, i
       // 256 words or more (measured faster than every other form on every such combine of the 13-
       // and 15-vertex trees on R-MAT 21; slower on rows of about a hundred words)
       const bool sched_default = shape == 0 && op.ld_a + (op.ema_sym ? 0 : op.ld_p) >= 256;
-      const bool sched2 = shape == kShapeEmaSched2;
+      // two blocks per SM by default where each gets at least the rows one block would
+      int upg0 = 1;
+      const bool sched2 = shape == kShapeEmaSched2 ||
+                          (sched_default && ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, smem_cap,
+                                                           &upg0, 2) >=
+                                                ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem,
+                                                               smem_cap, &upg0, 1));
       if (!op.ema_reg_k && batch == 1 && (shape == kShapeEmaSched || sched2 || sched_default)) {
         int upg = 1;
         const int r = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, elem, smem_cap, &upg, sched2 ? 2 : 1);
@@ -1338,7 +1345,7 @@ std::vector<int> op_shape_candidates(const sgc_graph* g, const Plan& P, int i) {
       c.insert(c.begin(), kShapeEmaSched);
       const int r1 = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg);
       const int r2 = ema_sched_rows(op.cols_out, op.ld_a, op.ld_p, op.ema_sym, P.elem, smem_cap, &upg, 2);
-      if (r2 > 0 && r2 < r1) c.insert(c.begin() + 1, kShapeEmaSched2);  // a different row count
+      if (r2 > 0 && r2 != r1) c.insert(c.begin() + 1, kShapeEmaSched2);  // a different row count
     }
   }
   if (c.size() < 2) c.clear();

@@ -260,9 +260,9 @@ constexpr int kShapeEmaVertex1 = 101, kShapeEmaVertex2 = 102, kShapeEmaReg = 103
 // the scheduled eMA (shape 104, one coloring per pass, kEmaSchedWarps warps per block): rows a block
 // stages (8, 6, 4 or 2 within 200 KB; 0 = does not fit) and shares of each group of 32 outputs' rounds
 constexpr int kEmaSchedWarps = 16;
-// rows per block of the scheduled eMA: the most of 8, 6, 4, 2 whose block fits in at most 200 KB
-// (blocks = 1) or in half of an SM's shared memory (blocks = 2: two blocks per SM, one staging its
-// rows while the other computes); 0 when none fits
+// rows per block of the scheduled eMA: the most of 8, 6, 4, 2 (12 too for two blocks) whose
+// block fits in at most 200 KB (blocks = 1) or in half of an SM's shared memory (blocks = 2: two
+// blocks per SM, one staging its rows while the other computes); 0 when none fits
 int ema_sched_rows(int64_t ct, int64_t ld_a, int64_t ld_p, bool sym, int elem, int64_t smem_cap, int* upg,
                    int blocks = 1);
 // words of one staged row: M_a row, P row (unless the table is combined with itself), 4 zero words
